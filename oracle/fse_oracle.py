@@ -18,9 +18,11 @@ Conventions (readings of the paper, all listed in the design doc):
   (Eq. E1 with Eq. 25).  The frequency ratios rho_j are held fixed, so the
   rotation R(rho) and the forcing phases do not depend on w_1.
 * The initial acceleration a_0 comes from the equation of motion at phi_1 = 0.
-* Per-step Newton (App. E): full Newton from the predictor
-  q + D u + D^2/2 a, stopping when ||dq||_inf <= tol * ||q_{k+1}||_inf
-  (at least one iteration); tol <= 0 means "exactly maxit iterations".
+* Per-step Newton (App. E): full Newton started from the previous
+  displacement q_k (the paper does not name a predictor; the constant one
+  is the robust choice for the stiff axial and membrane modes of FE models),
+  stopping when ||dq||_inf <= tol * ||q_{k+1}||_inf (at least one
+  iteration); tol <= 0 means "exactly maxit iterations".
 
 Parity status of each function is stated in its docstring.
 """
@@ -263,7 +265,7 @@ def integrate_trajectory(model, omega1, rho, phis, q0, u0, S1, tol=1e-10, maxit=
         S q_{k+1} + f_nl(q_{k+1}, w u_{k+1}(q_{k+1})) = b
         S = w^2 4/Delta^2 M + w 2/Delta D + K
         b = e_{k+1} + w^2 M (4/Delta^2 q_k + 4/Delta u_k + a_k) + w D (2/Delta q_k + u_k)
-    solved by full Newton with K_eff = S + K_t + w 2/Delta C_t.
+    solved by full Newton with K_eff = S + K_t + w 2/Delta C_t, started at q_k.
 
     Sensitivities (Eq. E8, E9) by differentiating the same step: with
     X = dq/dp, V = du/dp, W = da/dp for p in (q_0, u_0, w_1):
@@ -303,7 +305,7 @@ def integrate_trajectory(model, omega1, rho, phis, q0, u0, S1, tol=1e-10, maxit=
     for k in range(steps):
         phi_next = (k + 1) * Dl
         b = forcing(model, phi_next, phis, rho) + wM @ (a0c * q + a1c * u + a) + w * D @ (a2c * q + u)
-        qn = q + Dl * u + 0.5 * Dl * Dl * a           # predictor
+        qn = q.copy()                                  # predictor: previous displacement
         it = 0
         ok = False
         while it < maxit:
