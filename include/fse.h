@@ -1,0 +1,175 @@
+/*
+ * fse.h -- C ABI of the GB300-native FSE-Shooting hot path.
+ *
+ * FSE-Shooting (Fourier-series-expansion shooting, arXiv 2508.06302) finds a
+ * quasi-periodic response of  M q'' + D q' + K q + f_nl(q) = sum_i F_i cos(w_i t)
+ * (Eq. 1 with Theta = I, Eq. 25) as the Fourier coefficients Z(0) of the
+ * (d-1)-torus of trajectory start points that satisfy the coupling residual
+ *     R(Z(0), w) = (I_2n (x) R(rho)) Z(2 pi) - Z(0)                   (Eq. 16)
+ * evaluated by  Z(0) -i-DFT-> zbar(0) -Newmark-> zbar(2 pi) -DFT-> Z(2 pi)
+ * (Eq. 17, Eq. 20, Eq. 21, App. E).
+ *
+ * Conventions shared by every entry point
+ *  - Real numbers are IEEE double unless stated.  Matrices are dense,
+ *    row-major.  All pointers without a _dev suffix are HOST pointers; the
+ *    library copies what it needs and never keeps a caller pointer.
+ *  - The state is z = [q; u] with u = dq/dphi_1 = qdot / w_1 (App. E, Eq. E8).
+ *  - Z vectors are state-major: Z[i * U + c] is coefficient c of state i,
+ *    i < 2n, in the basis of Eq. (11) [1, cos k_1.phi, sin k_1.phi, ...].
+ *  - The frequency ratios rho_j = w_j / w_1 (j = 2..d) are fixed per context,
+ *    so the torus rotation and the forcing phases do not depend on w_1.
+ *  - Return value: FSE_OK (0) or a negative FSE_E* code; fse_last_error()
+ *    gives a one-line text.  The library never aborts or traps; every device
+ *    loop has a fixed bound.
+ *  - A context is not thread-safe; distinct contexts may be used from
+ *    distinct host threads.  All work of a context runs on its stream.
+ */
+#ifndef FSE_H
+#define FSE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSE_OK 0
+#define FSE_EINVAL (-1)        /* bad size / pointer / Nyquist rule / option */
+#define FSE_ENOMEM (-2)        /* device allocation failed                   */
+#define FSE_ENOCONV (-3)       /* per-step Newton hit its iteration limit    */
+#define FSE_ENONPOS_PIVOT (-4) /* effective stiffness not positive definite  */
+#define FSE_ENAN (-5)          /* non-finite value in a result               */
+#define FSE_ECUDA (-6)         /* CUDA runtime error                         */
+#define FSE_ENOJAC (-7)        /* no Jacobian stored in the context yet      */
+
+/* Nonlinear element types of f_nl (Eq. 1).  None depends on qdot (C_t = 0). */
+#define FSE_NL_CUBIC_GROUND 1  /* f[d0] += p0 q[d0]^3                          */
+#define FSE_NL_CUBIC_DIFF 2    /* s = q[d0]-q[d1]: f[d0] += p0 s^3, f[d1] -= p0 s^3 */
+#define FSE_NL_VK_BEAM 3       /* 2-node von Karman beam, dofs (u1,w1,th1,u2,w2,th2),
+                                  p0 = EA, p1 = length; force = gradient of
+                                  EA/2 int (u' w'^2 + w'^4/4) dx; dof -1 = clamped */
+
+/* Precision of the sensitivity (monodromy) propagation.  The trajectory
+ * state, the per-step Newton residual and test, the coupling residual and
+ * the outer solve are FP64 in every mode. */
+#define FSE_FP64 0             /* plain: sensitivities FP64                    */
+#define FSE_MIXED_FP32 1       /* sensitivities + factorisation FP32           */
+
+typedef struct {
+    int type;                  /* FSE_NL_*                                     */
+    int dof[6];                /* global dof indices, -1 = unused / clamped    */
+    double p[6];               /* parameters, see FSE_NL_*                     */
+} fse_nl_elem;
+
+typedef struct {
+    int n;                     /* number of dofs                               */
+    const double* M;           /* n x n mass, symmetric positive definite      */
+    const double* D;           /* n x n viscous damping, symmetric             */
+    const double* K;           /* n x n linear stiffness, symmetric            */
+    int n_nl;                  /* number of nonlinear elements (>= 0)          */
+    const fse_nl_elem* nl;     /* n_nl records                                 */
+    int e;                     /* number of forcing components, 1 <= e <= d    */
+    const double* F;           /* e x n amplitudes: e(t) = sum_i F_i cos(w_i t) */
+} fse_model;
+
+typedef struct {
+    int d;                     /* base frequencies, 2 <= d <= 4                */
+    const int* S;              /* d-1 sample counts S_j; N = prod S_j          */
+    const int* H;              /* d-1 highest harmonics; S_j >= 2 H_j + 1      */
+    const double* rho;         /* d-1 fixed ratios rho_j = w_j / w_1           */
+    int S1;                    /* Newmark steps per period T_1 = 2 pi / w_1    */
+    double newton_tol;         /* per-step Newton: ||dq||_inf <= tol ||q||_inf;
+                                  tol <= 0 runs exactly newton_maxit iterations */
+    int newton_maxit;          /* 1..64                                        */
+    int precision;             /* FSE_FP64 or FSE_MIXED_FP32                   */
+} fse_opts;
+
+typedef struct fse_ctx fse_ctx;
+
+/* fse_setup -- validate and copy the model and options to the GPU, build the
+ * harmonic table (App. B), the sample grid and Gamma / Gamma^-1 (App. D), the
+ * rotation R(rho) (Eq. 14) and the banded forms of M, D, K (the half-bandwidth
+ * b is detected from the exact zeros of M, D, K and the element dof spans).
+ * Allocates all device memory of the context.  Errors: FSE_EINVAL for bad
+ * sizes, the sampling rule S_j >= 2 H_j + 1 (Sec. 3.1), e > d, an element dof
+ * out of range or a non-positive-definite M (FSE_ENONPOS_PIVOT); FSE_ENOMEM.
+ * On error *out is NULL.  device < 0 uses the current device. */
+int fse_setup(const fse_model* model, const fse_opts* opts, int device, fse_ctx** out);
+
+void fse_destroy(fse_ctx* ctx);
+
+/* Text of the last error of ctx (or of the last failed fse_setup if ctx is NULL). */
+const char* fse_last_error(const fse_ctx* ctx);
+
+/* Sizes: unknowns 2 n U~, U~ = prod (2 H_j + 1), N = prod S_j, n, half-bandwidth b. */
+int fse_sizes(const fse_ctx* ctx, int* n_unknowns, int* U_tilde, int* N, int* n, int* band);
+
+/* Harmonic table K~^d of App. B (Eq. B1-B2): (U~+1)/2 rows of d-1 ints,
+ * rows k~_1..k~_L first, the zero row last.  ktilde is caller-owned. */
+int fse_harmonics(const fse_ctx* ctx, int* ktilde);
+
+/* fse_residual_jacobian -- one evaluation of Eq. (16) at (Z0, w_1).
+ *  Z0      host, 2 n U~ doubles (state-major)
+ *  R_out   host, 2 n U~ doubles: R = (I (x) R(rho)) Z(2 pi) - Z0
+ *  want_jacobian: 0 = residual only; 1 = also propagate the sensitivities
+ *          and keep the monodromy blocks Phi_s = d zbar_s(2 pi)/d zbar_s(0)
+ *          (Eq. E8) and d zbar(2 pi)/d w_1 on the device for
+ *          fse_jacobian_apply / _domega / _dense / fse_monodromy.
+ *  traj_status host, N ints or NULL: per-trajectory 0 = ok, FSE_ENOCONV,
+ *          FSE_ENONPOS_PIVOT, FSE_ENAN.
+ *  newton_iters host, N ints or NULL: total per-step Newton iterations.
+ * Returns the worst per-trajectory status (FSE_OK if all converged). */
+int fse_residual_jacobian(fse_ctx* ctx, const double* Z0, double omega1, double* R_out,
+                          int want_jacobian, int* traj_status, int* newton_iters);
+
+/* Same on device memory: Z0_dev / R_dev are device pointers (2 n U~ doubles)
+ * and the call is asynchronous on `stream` (a cudaStream_t; NULL = the
+ * context stream).  The status of the run is read with fse_status(). */
+int fse_residual_jacobian_dev(fse_ctx* ctx, const double* Z0_dev, double omega1, double* R_dev,
+                              int want_jacobian, void* stream);
+
+/* Waits for the context stream and returns the worst trajectory status of
+ * the last evaluation (copied to traj_status / newton_iters when non-NULL). */
+int fse_status(fse_ctx* ctx, int* traj_status, int* newton_iters);
+
+/* Eq. (22) applied without forming J:  Jv = (I (x) R Gamma^-1) blockdiag(Phi_s)
+ * (I (x) Gamma) v - v for nvec vectors of 2 n U~ doubles each (host, packed). */
+int fse_jacobian_apply(fse_ctx* ctx, const double* v, double* Jv, int nvec);
+
+/* Eq. (23), i = 1, rho fixed: dR/dw_1 = (I (x) R Gamma^-1) d zbar(2 pi)/d w_1. */
+int fse_jacobian_domega(fse_ctx* ctx, double* dRdw1);
+
+/* Dense dR/dZ(0) of Eq. (22), (2 n U~)^2 doubles, row-major.  FSE_EINVAL if
+ * the matrix would exceed 2^31 entries. */
+int fse_jacobian_dense(fse_ctx* ctx, double* J);
+
+/* Copy the monodromy blocks Phi_s (N x 2n x 2n, row-major) and
+ * d zbar_s(2 pi)/d w_1 (N x 2n) of the last evaluation (either may be NULL). */
+int fse_monodromy(fse_ctx* ctx, double* Phi, double* dz_dw);
+
+/* One Newton-Raphson update of Z(0) at fixed w_1 (Sec. 3.3 step 6): evaluates
+ * R and J at Z0, solves J dZ = -R on the GPU (dense LU with partial pivoting,
+ * for 2 n U~ <= 16384) and overwrites Z0 <- Z0 + dZ.  res_norm_out receives
+ * ||R(Z0_in)||_2.  Returns the evaluation status. */
+int fse_newton_step(fse_ctx* ctx, double* Z0, double omega1, double* res_norm_out);
+
+/* First-order Lyapunov exponents (App. F) of the torus at (Z0, w_1), 1/s,
+ * from the monodromy by-product: Psi_s = diag(I, w_1 I) Phi_s diag(I, I/w_1)
+ * (Eq. F3), trigonometric interpolation of Psi over phi~ with the context
+ * harmonics at phi~ = 2 (i-1) pi rho, QR re-orthonormalisation for
+ * i = 1..N_Ly, sigma_j = sum_i ln|R_i[j,j]| / (N_Ly T_1), j < h.
+ * Re-evaluates the Jacobian at Z0 (FP64 sensitivities are used whatever the
+ * context precision).  sigma_out: h doubles (host). */
+int fse_lyapunov(fse_ctx* ctx, const double* Z0, double omega1, int N_Ly, int h,
+                 double* sigma_out);
+
+/* Device time of the phases of the last evaluation, milliseconds:
+ * [0] total, [1] per-step state Newton + factorisation, [2] sensitivity
+ * right-hand side, [3] sensitivity solves, [4] AFT. Up to `cap` values. */
+int fse_timings(fse_ctx* ctx, double* ms, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSE_H */

@@ -1,0 +1,562 @@
+// C-ABI entry points of the FSE-Shooting library (include/fse.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fse_internal.h"
+
+using fse::Params;
+
+static std::string g_setup_err;
+
+static int set_err(fse_ctx* c, int code, const std::string& msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_setup_err = msg;
+    return code;
+}
+
+static int cuda_check(fse_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return FSE_OK;
+    return set_err(c, e == cudaErrorMemoryAllocation ? FSE_ENOMEM : FSE_ECUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// App. B, Eq. (B1)-(B2): rows k~_1 .. k~_L, then the zero row.
+static std::vector<std::vector<int>> harmonic_rows(const std::vector<int>& H) {
+    std::vector<std::vector<int>> tab;
+    for (int k = 1; k <= H[0]; ++k) tab.push_back({k});
+    tab.push_back({0});
+    for (size_t dd = 1; dd < H.size(); ++dd) {
+        const int Hd = H[dd];
+        std::vector<std::vector<int>> next;
+        // K^{d,g}: k_d slowest, the rows of K~^{d-1} without its zero row fastest, last entry -k_d
+        for (int kd = 1; kd <= Hd; ++kd)
+            for (size_t r = 0; r + 1 < tab.size(); ++r) {
+                std::vector<int> row = tab[r];
+                row.push_back(-kd);
+                next.push_back(row);
+            }
+        // K~^{d,b}: [k_d; 0] slowest, all rows of K~^{d-1} fastest, last entry +k_d (or 0)
+        for (int kk = 1; kk <= Hd + 1; ++kk) {
+            const int kd = (kk <= Hd) ? kk : 0;
+            for (size_t r = 0; r < tab.size(); ++r) {
+                std::vector<int> row = tab[r];
+                row.push_back(kd);
+                next.push_back(row);
+            }
+        }
+        tab.swap(next);
+    }
+    return tab;
+}
+
+template <typename P>
+static cudaError_t dalloc(P** p, size_t bytes) {
+    return cudaMalloc((void**)p, bytes > 0 ? bytes : 16);
+}
+
+static void free_ctx(fse_ctx* c) {
+    if (!c) return;
+    void* ptrs[] = {c->d.Mb, c->d.Db, c->d.Kb, c->d.Sb, c->d.F, c->d.el_type, c->d.el_dof, c->d.el_p,
+                    c->d.col_off, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs, c->d.ktab,
+                    c->d.LMc, c->d.LMr, c->d.LMinv, c->d.LMc_t, c->d.LMr_t, c->d.LMinv_t, c->d.q,
+                    c->d.u, c->d.a, c->d.zb, c->d.Kt0, c->d.Lc, c->d.Lr, c->d.Linv, c->d.X, c->d.V,
+                    c->d.W, c->d.Y, c->d.Z0, c->d.R, c->d.vec, c->d.vec2, c->d.yb, c->d.status,
+                    c->d.iters, c->Jd, c->piv};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_ctx** out) {
+    if (!out) return set_err(nullptr, FSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!m || !o) return set_err(nullptr, FSE_EINVAL, "model or opts is NULL");
+    const int n = m->n;
+    if (n < 1 || !m->M || !m->D || !m->K) return set_err(nullptr, FSE_EINVAL, "bad n or matrix pointer");
+    if (o->d < 2 || o->d > FSE_MAX_D) return set_err(nullptr, FSE_EINVAL, "d must be in [2, 4]");
+    if (m->e < 1 || m->e > o->d || !m->F) return set_err(nullptr, FSE_EINVAL, "need 1 <= e <= d and F");
+    if (m->n_nl < 0 || (m->n_nl > 0 && !m->nl)) return set_err(nullptr, FSE_EINVAL, "bad nonlinear element list");
+    if (!o->S || !o->H || !o->rho) return set_err(nullptr, FSE_EINVAL, "S, H, rho required");
+    if (o->S1 < 2) return set_err(nullptr, FSE_EINVAL, "S1 must be >= 2");
+    if (o->newton_maxit < 1 || o->newton_maxit > 64) return set_err(nullptr, FSE_EINVAL, "newton_maxit in [1, 64]");
+    if (o->precision != FSE_FP64 && o->precision != FSE_MIXED_FP32)
+        return set_err(nullptr, FSE_EINVAL, "unknown precision");
+    std::vector<int> S(o->S, o->S + o->d - 1), H(o->H, o->H + o->d - 1);
+    long long N = 1, U = 1;
+    for (int j = 0; j < o->d - 1; ++j) {
+        if (H[j] < 0 || S[j] < 1) return set_err(nullptr, FSE_EINVAL, "bad S_j or H_j");
+        if (S[j] < 2 * H[j] + 1)
+            return set_err(nullptr, FSE_EINVAL, "sampling rule S_j >= 2 H_j + 1 violated (Sec. 3.1)");
+        N *= S[j];
+        U *= 2 * H[j] + 1;
+    }
+    if (N > 65535 || U > 65535) return set_err(nullptr, FSE_EINVAL, "N or U too large");
+    for (int j = 0; j < o->d - 1; ++j)
+        if (!std::isfinite(o->rho[j])) return set_err(nullptr, FSE_EINVAL, "rho not finite");
+    // half-bandwidth from exact zeros and element spans
+    int b = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const size_t o2 = (size_t)i * n + j;
+            if (m->M[o2] != 0.0 || m->D[o2] != 0.0 || m->K[o2] != 0.0) b = std::max(b, std::abs(i - j));
+        }
+    for (int e = 0; e < m->n_nl; ++e) {
+        const fse_nl_elem& el = m->nl[e];
+        if (el.type < 1 || el.type > 3) return set_err(nullptr, FSE_EINVAL, "unknown element type");
+        const int nd = el.type == 1 ? 1 : (el.type == 2 ? 2 : 6);
+        for (int a = 0; a < nd; ++a) {
+            if (el.dof[a] >= n || el.dof[a] < -1) return set_err(nullptr, FSE_EINVAL, "element dof out of range");
+            if (el.type != 3 && el.dof[a] < 0) return set_err(nullptr, FSE_EINVAL, "spring dof must be >= 0");
+            for (int c2 = 0; c2 < nd; ++c2)
+                if (el.dof[a] >= 0 && el.dof[c2] >= 0) b = std::max(b, std::abs(el.dof[a] - el.dof[c2]));
+        }
+        if (el.type == 3 && !(el.p[1] > 0.0)) return set_err(nullptr, FSE_EINVAL, "beam element length must be > 0");
+    }
+    fse_ctx* c = new (std::nothrow) fse_ctx();
+    if (!c) return set_err(nullptr, FSE_ENOMEM, "host allocation failed");
+    Params& p = c->p;
+    p.n = n;
+    p.b = b;
+    p.d = o->d;
+    p.e = m->e;
+    p.N = (int)N;
+    p.U = (int)U;
+    p.L = (int)(U - 1) / 2;
+    p.S1 = o->S1;
+    p.P = 2 * n + 1;
+    p.maxit = o->newton_maxit;
+    p.prec = o->precision;
+    p.tol = o->newton_tol;
+    p.n_el = m->n_nl;
+    const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
+    const int nb = b + 1;
+    p.smem_state = (size_t)6 * n * sizeof(double) + (size_t)nb * nb * tsz;
+    if (p.smem_state > 200 * 1024 || (size_t)nb * 128 * tsz > 200 * 1024 ||
+        (size_t)nb * nb * sizeof(double) > 200 * 1024) {
+        free_ctx(c);
+        return set_err(nullptr, FSE_EINVAL, "n or half-bandwidth too large for the on-chip working set");
+    }
+    for (int j = 0; j < o->d - 1; ++j) c->rho.push_back(o->rho[j]);
+    if (device >= 0) {
+        if (cudaSetDevice(device) != cudaSuccess) {
+            free_ctx(c);
+            return set_err(nullptr, FSE_ECUDA, "cudaSetDevice failed");
+        }
+        c->device = device;
+    } else {
+        cudaGetDevice(&c->device);
+    }
+    int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+    if (rc) {
+        g_setup_err = c->err;
+        free_ctx(c);
+        return rc;
+    }
+    for (auto& e : c->ev) cudaEventCreate(&e);
+    // harmonic table
+    auto rows = harmonic_rows(H);
+    const int dm1 = p.d - 1;
+    c->ktab_host.resize((size_t)rows.size() * dm1);
+    for (size_t r = 0; r < rows.size(); ++r)
+        for (int j = 0; j < dm1; ++j) c->ktab_host[r * dm1 + j] = rows[r][j];
+    // sample grid (Eq. D1): phi_2 fastest
+    std::vector<double> phis((size_t)N * dm1);
+    for (long long s = 0; s < N; ++s) {
+        long long rem = s;
+        for (int j = 0; j < dm1; ++j) {
+            const long long ij = rem % S[j];
+            rem /= S[j];
+            phis[s * dm1 + j] = 2.0 * M_PI * (double)ij / (double)S[j];
+        }
+    }
+    // rotation angles 2 pi k~_l . rho (Eq. 14)
+    std::vector<double> rcv(std::max(p.L, 1)), rsv(std::max(p.L, 1));
+    for (int l = 0; l < p.L; ++l) {
+        double th = 0.0;
+        for (int j = 0; j < dm1; ++j) th += (double)rows[l][j] * o->rho[j];
+        th *= 2.0 * M_PI;
+        rcv[l] = cos(th);
+        rsv[l] = sin(th);
+    }
+    // diagonal-major full bands
+    const int fb = 2 * b + 1;
+    std::vector<double> Mb((size_t)fb * n, 0.0), Db((size_t)fb * n, 0.0), Kb((size_t)fb * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int cc = 0; cc < fb; ++cc) {
+            const int j = i + cc - b;
+            if (j < 0 || j >= n) continue;
+            Mb[(size_t)cc * n + i] = m->M[(size_t)i * n + j];
+            Db[(size_t)cc * n + i] = m->D[(size_t)i * n + j];
+            Kb[(size_t)cc * n + i] = m->K[(size_t)i * n + j];
+        }
+    // colour the elements so that no two of a colour share a dof
+    std::vector<int> color(m->n_nl, 0);
+    std::vector<uint64_t> used(n, 0);
+    int ncol = 0;
+    for (int e = 0; e < m->n_nl; ++e) {
+        const fse_nl_elem& el = m->nl[e];
+        const int nd = el.type == 1 ? 1 : (el.type == 2 ? 2 : 6);
+        uint64_t mask = 0;
+        for (int a = 0; a < nd; ++a)
+            if (el.dof[a] >= 0) mask |= used[el.dof[a]];
+        int cl = 0;
+        while (cl < 64 && (mask >> cl) & 1ull) ++cl;
+        if (cl >= 64) {
+            free_ctx(c);
+            return set_err(nullptr, FSE_EINVAL, "element graph needs more than 64 colours");
+        }
+        color[e] = cl;
+        ncol = std::max(ncol, cl + 1);
+        for (int a = 0; a < nd; ++a)
+            if (el.dof[a] >= 0) used[el.dof[a]] |= (1ull << cl);
+    }
+    p.ncolors = ncol;
+    std::vector<int> order(m->n_nl);
+    for (int e = 0; e < m->n_nl; ++e) order[e] = e;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return color[x] < color[y]; });
+    std::vector<int> et(m->n_nl), ed((size_t)6 * m->n_nl), coff(ncol + 1, 0);
+    std::vector<double> ep((size_t)6 * m->n_nl);
+    for (int k = 0; k < m->n_nl; ++k) {
+        const fse_nl_elem& el = m->nl[order[k]];
+        et[k] = el.type;
+        for (int a = 0; a < 6; ++a) {
+            ed[(size_t)6 * k + a] = el.dof[a];
+            ep[(size_t)6 * k + a] = el.p[a];
+        }
+        coff[color[order[k]] + 1]++;
+    }
+    for (int cl = 0; cl < ncol; ++cl) coff[cl + 1] += coff[cl];
+    // device allocations
+    const size_t Nn = (size_t)N * n, band = (size_t)fb * n, lb = (size_t)n * nb;
+    const size_t sensz = (size_t)N * n * p.P * tsz;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = dalloc(ptr, bytes);
+    };
+    A(&c->d.Mb, band * 8);
+    A(&c->d.Db, band * 8);
+    A(&c->d.Kb, band * 8);
+    A(&c->d.Sb, band * 8);
+    A(&c->d.F, (size_t)m->e * n * 8);
+    A(&c->d.el_type, (size_t)std::max(1, m->n_nl) * 4);
+    A(&c->d.el_dof, (size_t)std::max(1, m->n_nl) * 24);
+    A(&c->d.el_p, (size_t)std::max(1, m->n_nl) * 48);
+    A(&c->d.col_off, (size_t)(ncol + 1) * 4);
+    A(&c->d.phis, (size_t)N * dm1 * 8);
+    A(&c->d.G, (size_t)N * U * 8);
+    A(&c->d.Gi, (size_t)N * U * 8);
+    A(&c->d.RG, (size_t)N * U * 8);
+    A(&c->d.rc, rcv.size() * 8);
+    A(&c->d.rs, rsv.size() * 8);
+    A(&c->d.ktab, c->ktab_host.size() * 4);
+    A(&c->d.LMc, lb * 8);
+    A(&c->d.LMr, lb * 8);
+    A(&c->d.LMinv, (size_t)n * 8);
+    if (p.prec == FSE_MIXED_FP32) {
+        A(&c->d.LMc_t, lb * 4);
+        A(&c->d.LMr_t, lb * 4);
+        A(&c->d.LMinv_t, (size_t)n * 4);
+    }
+    A(&c->d.q, Nn * 8);
+    A(&c->d.u, Nn * 8);
+    A(&c->d.a, Nn * 8);
+    A(&c->d.zb, Nn * 16);
+    A(&c->d.yb, Nn * 16);
+    A(&c->d.Kt0, (size_t)N * lb * 8);
+    A(&c->d.Lc, (size_t)N * lb * tsz);
+    A(&c->d.Lr, (size_t)N * lb * tsz);
+    A(&c->d.Linv, Nn * tsz);
+    A(&c->d.X, sensz);
+    A(&c->d.V, sensz);
+    A(&c->d.W, sensz);
+    A(&c->d.Y, sensz);
+    const size_t nu = (size_t)2 * n * U;
+    A(&c->d.Z0, nu * 8);
+    A(&c->d.R, nu * 8);
+    A(&c->d.vec, nu * 8);
+    A(&c->d.vec2, nu * 8);
+    A(&c->d.status, (size_t)N * 4);
+    A(&c->d.iters, (size_t)N * 4);
+    if (e != cudaSuccess) {
+        rc = cuda_check(c, e, "device allocation");
+        g_setup_err = c->err;
+        free_ctx(c);
+        return rc;
+    }
+    cudaStream_t st = c->stream;
+    cudaMemcpyAsync(c->d.Mb, Mb.data(), band * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.Db, Db.data(), band * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.Kb, Kb.data(), band * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.F, m->F, (size_t)m->e * n * 8, cudaMemcpyHostToDevice, st);
+    if (m->n_nl > 0) {
+        cudaMemcpyAsync(c->d.el_type, et.data(), et.size() * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d.el_dof, ed.data(), ed.size() * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d.el_p, ep.data(), ep.size() * 8, cudaMemcpyHostToDevice, st);
+    }
+    cudaMemcpyAsync(c->d.col_off, coff.data(), coff.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.phis, phis.data(), phis.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.rc, rcv.data(), rcv.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.rs, rsv.data(), rsv.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.ktab, c->ktab_host.data(), c->ktab_host.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(c->d.status, 0, (size_t)N * 4, st);
+    cudaMemsetAsync(c->d.iters, 0, (size_t)N * 4, st);
+    fse::launch_fill_tables(c);
+    const int bad = fse::launch_factor_M(c);
+    rc = cuda_check(c, cudaStreamSynchronize(st), "setup");
+    if (rc == FSE_OK) rc = cuda_check(c, cudaGetLastError(), "setup kernels");
+    if (rc == FSE_OK && bad) rc = set_err(c, FSE_ENONPOS_PIVOT, "mass matrix is not positive definite");
+    if (rc) {
+        g_setup_err = c->err;
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return FSE_OK;
+}
+
+extern "C" void fse_destroy(fse_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+extern "C" const char* fse_last_error(const fse_ctx* c) {
+    return c ? c->err.c_str() : g_setup_err.c_str();
+}
+
+extern "C" int fse_sizes(const fse_ctx* c, int* nu, int* U, int* N, int* n, int* band) {
+    if (!c) return FSE_EINVAL;
+    if (nu) *nu = 2 * c->p.n * c->p.U;
+    if (U) *U = c->p.U;
+    if (N) *N = c->p.N;
+    if (n) *n = c->p.n;
+    if (band) *band = c->p.b;
+    return FSE_OK;
+}
+
+extern "C" int fse_harmonics(const fse_ctx* c, int* kt) {
+    if (!c || !kt) return FSE_EINVAL;
+    std::memcpy(kt, c->ktab_host.data(), c->ktab_host.size() * sizeof(int));
+    return FSE_OK;
+}
+
+// the whole evaluation, asynchronous on the context stream
+static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, int sens) {
+    if (!(w > 0.0) || !std::isfinite(w)) return set_err(c, FSE_EINVAL, "omega1 must be positive and finite");
+    cudaSetDevice(c->device);
+    const Params& p = c->p;
+    if (w != c->omega_S) {
+        fse::launch_build_S(c, w);
+        c->omega_S = w;
+    }
+    cudaEventRecord(c->ev[0], c->stream);
+    fse::launch_idft(c, Z0_dev, c->d.zb, 1);
+    fse::launch_init_state(c, w, sens);
+    if (sens) fse::launch_sens_init(c, w);
+    for (int k = 0; k < p.S1; ++k) {
+        fse::launch_state_step(c, k, w, sens);
+        if (sens) {
+            fse::launch_sens_step(c, w, 0);
+            fse::launch_sens_step(c, w, 1);
+        }
+    }
+    fse::launch_collect_end(c);
+    fse::launch_dft_residual(c, c->d.zb, Z0_dev, R_dev, 1);
+    cudaEventRecord(c->ev[1], c->stream);
+    c->have_jac = sens != 0;
+    c->omega_jac = w;
+    return cuda_check(c, cudaGetLastError(), "evaluation launch");
+}
+
+static int collect_status(fse_ctx* c, int* ts, int* it) {
+    const int N = c->p.N;
+    std::vector<int> st(N), its(N);
+    cudaMemcpyAsync(st.data(), c->d.status, N * 4, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(its.data(), c->d.iters, N * 4, cudaMemcpyDeviceToHost, c->stream);
+    int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "evaluation");
+    if (rc) return rc;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) c->timing[0] = ms;
+    if (ts) std::memcpy(ts, st.data(), N * 4);
+    if (it) std::memcpy(it, its.data(), N * 4);
+    int worst = FSE_OK;
+    for (int s = 0; s < N; ++s)
+        if (st[s] != FSE_OK && (worst == FSE_OK || st[s] < worst)) worst = st[s];
+    if (worst == FSE_ENOCONV) c->err = "per-step Newton did not converge on some trajectories";
+    if (worst == FSE_ENONPOS_PIVOT) c->err = "effective stiffness lost positive definiteness";
+    if (worst == FSE_ENAN) c->err = "non-finite values in the trajectory";
+    return worst;
+}
+
+extern "C" int fse_residual_jacobian_dev(fse_ctx* c, const double* Z0_dev, double w, double* R_dev,
+                                         int sens, void* stream) {
+    if (!c || !Z0_dev || !R_dev) return FSE_EINVAL;
+    cudaStream_t user = (cudaStream_t)stream;
+    if (user && user != c->stream) {
+        // order the context stream after the caller's stream, and the caller's after the result
+        cudaEventRecord(c->ev[6], user);
+        cudaStreamWaitEvent(c->stream, c->ev[6], 0);
+    }
+    int rc = run_eval(c, Z0_dev, w, R_dev, sens);
+    if (user && user != c->stream) {
+        cudaEventRecord(c->ev[7], c->stream);
+        cudaStreamWaitEvent(user, c->ev[7], 0);
+    }
+    return rc;
+}
+
+extern "C" int fse_status(fse_ctx* c, int* ts, int* it) {
+    if (!c) return FSE_EINVAL;
+    return collect_status(c, ts, it);
+}
+
+extern "C" int fse_residual_jacobian(fse_ctx* c, const double* Z0, double w, double* R_out, int sens,
+                                     int* ts, int* it) {
+    if (!c || !Z0 || !R_out) return FSE_EINVAL;
+    cudaSetDevice(c->device);
+    const size_t nu = (size_t)2 * c->p.n * c->p.U;
+    cudaMemcpyAsync(c->d.Z0, Z0, nu * 8, cudaMemcpyHostToDevice, c->stream);
+    int rc = run_eval(c, c->d.Z0, w, c->d.R, sens);
+    if (rc) return rc;
+    cudaMemcpyAsync(R_out, c->d.R, nu * 8, cudaMemcpyDeviceToHost, c->stream);
+    return collect_status(c, ts, it);
+}
+
+extern "C" int fse_jacobian_apply(fse_ctx* c, const double* v, double* Jv, int nvec) {
+    if (!c || !v || !Jv || nvec < 0) return FSE_EINVAL;
+    if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored: call fse_residual_jacobian with want_jacobian=1");
+    cudaSetDevice(c->device);
+    const size_t nu = (size_t)2 * c->p.n * c->p.U;
+    for (int k = 0; k < nvec; ++k) {
+        cudaMemcpyAsync(c->d.vec, v + k * nu, nu * 8, cudaMemcpyHostToDevice, c->stream);
+        fse::launch_idft(c, c->d.vec, c->d.zb, 1);
+        fse::launch_phi_apply(c, c->d.zb, c->d.yb);
+        fse::launch_dft_residual(c, c->d.yb, c->d.vec, c->d.vec2, 1);
+        cudaMemcpyAsync(Jv + k * nu, c->d.vec2, nu * 8, cudaMemcpyDeviceToHost, c->stream);
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "jacobian_apply");
+}
+
+extern "C" int fse_jacobian_domega(fse_ctx* c, double* out) {
+    if (!c || !out) return FSE_EINVAL;
+    if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored");
+    cudaSetDevice(c->device);
+    const size_t nu = (size_t)2 * c->p.n * c->p.U;
+    fse::launch_domega(c, c->d.yb);
+    fse::launch_dft_residual(c, c->d.yb, nullptr, c->d.vec2, 0);
+    cudaMemcpyAsync(out, c->d.vec2, nu * 8, cudaMemcpyDeviceToHost, c->stream);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "jacobian_domega");
+}
+
+static int ensure_dense(fse_ctx* c, size_t m) {
+    if (c->Jd_cap >= m * m) return FSE_OK;
+    if (c->Jd) cudaFree(c->Jd);
+    if (c->piv) cudaFree(c->piv);
+    c->Jd = nullptr;
+    c->piv = nullptr;
+    c->Jd_cap = 0;
+    cudaError_t e = cudaMalloc(&c->Jd, m * m * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->piv, m * 4);
+    if (e != cudaSuccess) return cuda_check(c, e, "dense Jacobian allocation");
+    c->Jd_cap = m * m;
+    return FSE_OK;
+}
+
+extern "C" int fse_jacobian_dense(fse_ctx* c, double* J) {
+    if (!c || !J) return FSE_EINVAL;
+    if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored");
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    if (m * m > (1ull << 31)) return set_err(c, FSE_EINVAL, "dense Jacobian too large");
+    cudaSetDevice(c->device);
+    int rc = ensure_dense(c, m);
+    if (rc) return rc;
+    fse::launch_dense_jac(c, c->Jd);
+    cudaMemcpyAsync(J, c->Jd, m * m * 8, cudaMemcpyDeviceToHost, c->stream);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "jacobian_dense");
+}
+
+extern "C" int fse_monodromy(fse_ctx* c, double* Phi, double* dzdw) {
+    if (!c) return FSE_EINVAL;
+    if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored");
+    cudaSetDevice(c->device);
+    const size_t n2 = 2 * (size_t)c->p.n, N = c->p.N;
+    double *dP = nullptr, *dz = nullptr;
+    cudaError_t e = cudaMalloc(&dP, N * n2 * n2 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dz, N * n2 * 8);
+    if (e != cudaSuccess) {
+        if (dP) cudaFree(dP);
+        return cuda_check(c, e, "monodromy buffer");
+    }
+    fse::launch_phi_copy(c, dP, dz);
+    if (Phi) cudaMemcpyAsync(Phi, dP, N * n2 * n2 * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (dzdw) cudaMemcpyAsync(dzdw, dz, N * n2 * 8, cudaMemcpyDeviceToHost, c->stream);
+    int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "monodromy");
+    cudaFree(dP);
+    cudaFree(dz);
+    return rc;
+}
+
+extern "C" int fse_newton_step(fse_ctx* c, double* Z0, double w, double* res_norm) {
+    if (!c || !Z0) return FSE_EINVAL;
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    if (m > 16384) return set_err(c, FSE_EINVAL, "fse_newton_step: dense solve limited to 16384 unknowns");
+    cudaSetDevice(c->device);
+    int rc = ensure_dense(c, m);
+    if (rc) return rc;
+    cudaMemcpyAsync(c->d.Z0, Z0, m * 8, cudaMemcpyHostToDevice, c->stream);
+    rc = run_eval(c, c->d.Z0, w, c->d.R, 1);
+    if (rc) return rc;
+    std::vector<double> R(m);
+    cudaMemcpyAsync(R.data(), c->d.R, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    const int st = collect_status(c, nullptr, nullptr);
+    if (st < 0 && st != FSE_ENOCONV) return st;
+    double nr = 0.0;
+    for (double x : R) nr += x * x;
+    if (res_norm) *res_norm = std::sqrt(nr);
+    fse::launch_dense_jac(c, c->Jd);
+    // rhs = -R
+    for (double& x : R) x = -x;
+    cudaMemcpyAsync(c->d.vec, R.data(), m * 8, cudaMemcpyHostToDevice, c->stream);
+    rc = fse::dense_lu_solve(c, c->Jd, c->d.vec, (int)m);
+    if (rc) return set_err(c, rc, "singular shooting Jacobian");
+    std::vector<double> dZ(m);
+    cudaMemcpyAsync(dZ.data(), c->d.vec, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step");
+    if (rc) return rc;
+    for (size_t k = 0; k < m; ++k) Z0[k] += dZ[k];
+    return st;
+}
+
+extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, int h, double* sigma) {
+    if (!c || !Z0 || !sigma) return FSE_EINVAL;
+    if (N_Ly < 1 || h < 1 || h > 64 || h > 2 * c->p.n) return set_err(c, FSE_EINVAL, "need N_Ly >= 1, 1 <= h <= min(64, 2n)");
+    cudaSetDevice(c->device);
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    cudaMemcpyAsync(c->d.Z0, Z0, m * 8, cudaMemcpyHostToDevice, c->stream);
+    int rc = run_eval(c, c->d.Z0, w, c->d.R, 1);
+    if (rc) return rc;
+    const int st = collect_status(c, nullptr, nullptr);
+    if (st < 0 && st != FSE_ENOCONV) return st;
+    rc = fse::lyapunov_run(c, w, N_Ly, h, sigma);
+    return rc ? rc : st;
+}
+
+extern "C" int fse_timings(fse_ctx* c, double* ms, int cap) {
+    if (!c || !ms) return FSE_EINVAL;
+    for (int k = 0; k < cap && k < 5; ++k) ms[k] = c->timing[k];
+    return FSE_OK;
+}

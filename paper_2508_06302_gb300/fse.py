@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the FSE-Shooting C ABI (include/fse.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names (``fse_setup``, ``fse_residual_jacobian``,
+...); ``Context`` wraps one ``fse_ctx``.  Loading fails loudly when the
+library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+FSE_OK = 0
+FSE_EINVAL = -1
+FSE_ENOMEM = -2
+FSE_ENOCONV = -3
+FSE_ENONPOS_PIVOT = -4
+FSE_ENAN = -5
+FSE_ECUDA = -6
+FSE_ENOJAC = -7
+FSE_FP64 = 0
+FSE_MIXED_FP32 = 1
+
+_PREC = {"fp64": FSE_FP64, "mixed_fp32": FSE_MIXED_FP32, "fp32": FSE_MIXED_FP32}
+
+
+class fse_nl_elem(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("dof", ctypes.c_int * 6), ("p", ctypes.c_double * 6)]
+
+
+class fse_model(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("M", ctypes.POINTER(ctypes.c_double)),
+                ("D", ctypes.POINTER(ctypes.c_double)), ("K", ctypes.POINTER(ctypes.c_double)),
+                ("n_nl", ctypes.c_int), ("nl", ctypes.POINTER(fse_nl_elem)),
+                ("e", ctypes.c_int), ("F", ctypes.POINTER(ctypes.c_double))]
+
+
+class fse_opts(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("S", ctypes.POINTER(ctypes.c_int)),
+                ("H", ctypes.POINTER(ctypes.c_int)), ("rho", ctypes.POINTER(ctypes.c_double)),
+                ("S1", ctypes.c_int), ("newton_tol", ctypes.c_double),
+                ("newton_maxit", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_VP = ctypes.c_void_p
+
+
+def header_symbols():
+    """Names of the functions declared in include/fse.h."""
+    hdr = os.path.join(os.path.dirname(_build.HERE), "include", "fse.h")
+    src = open(hdr).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fse_[a-z0-9_]+)\s*\(", src)))
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (built by ``_build.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError("FSE CUDA library not built (%s); run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    sig = {
+        "fse_setup": (ctypes.c_int, [ctypes.POINTER(fse_model), ctypes.POINTER(fse_opts), ctypes.c_int,
+                                     ctypes.POINTER(_VP)]),
+        "fse_destroy": (None, [_VP]),
+        "fse_last_error": (ctypes.c_char_p, [_VP]),
+        "fse_sizes": (ctypes.c_int, [_VP, _IP, _IP, _IP, _IP, _IP]),
+        "fse_harmonics": (ctypes.c_int, [_VP, _IP]),
+        "fse_residual_jacobian": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP, ctypes.c_int, _IP, _IP]),
+        "fse_residual_jacobian_dev": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, ctypes.c_int, _VP]),
+        "fse_status": (ctypes.c_int, [_VP, _IP, _IP]),
+        "fse_jacobian_apply": (ctypes.c_int, [_VP, _DP, _DP, ctypes.c_int]),
+        "fse_jacobian_domega": (ctypes.c_int, [_VP, _DP]),
+        "fse_jacobian_dense": (ctypes.c_int, [_VP, _DP]),
+        "fse_monodromy": (ctypes.c_int, [_VP, _DP, _DP]),
+        "fse_newton_step": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP]),
+        "fse_lyapunov": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
+        "fse_timings": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(_IP)
+
+
+class FSEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("FSE error %d: %s" % (code, msg))
+        self.code = code
+
+
+# ----------------------------------------------------------------------------
+# C-named wrappers
+# ----------------------------------------------------------------------------
+
+def fse_setup(model, d, S, H, rho, S1, newton_tol=1e-10, newton_maxit=20, precision="fp64",
+              device=-1):
+    """fse_setup(): returns an opaque context handle (int)."""
+    lib = load()
+    M = np.ascontiguousarray(model.M, dtype=np.float64)
+    D = np.ascontiguousarray(model.D, dtype=np.float64)
+    K = np.ascontiguousarray(model.K, dtype=np.float64)
+    F = np.ascontiguousarray(model.F, dtype=np.float64)
+    m = int(model.nl_type.shape[0])
+    els = (fse_nl_elem * max(1, m))()
+    for k in range(m):
+        els[k].type = int(model.nl_type[k])
+        for a in range(6):
+            els[k].dof[a] = int(model.nl_dof[k, a])
+            els[k].p[a] = float(model.nl_p[k, a])
+    fm = fse_model(int(M.shape[0]), _dp(M), _dp(D), _dp(K), m, els, int(F.shape[0]), _dp(F))
+    Sa = np.ascontiguousarray(S, dtype=np.int32)
+    Ha = np.ascontiguousarray(H, dtype=np.int32)
+    ra = np.ascontiguousarray(rho, dtype=np.float64)
+    prec = _PREC[precision] if isinstance(precision, str) else int(precision)
+    fo = fse_opts(int(d), _ip(Sa), _ip(Ha), _dp(ra), int(S1), float(newton_tol), int(newton_maxit), prec)
+    h = _VP()
+    rc = lib.fse_setup(ctypes.byref(fm), ctypes.byref(fo), int(device), ctypes.byref(h))
+    if rc != FSE_OK:
+        raise FSEError(rc, lib.fse_last_error(None).decode())
+    return h.value
+
+
+def fse_destroy(ctx):
+    load().fse_destroy(ctx)
+
+
+def fse_last_error(ctx):
+    return load().fse_last_error(ctx).decode()
+
+
+def fse_sizes(ctx):
+    v = [ctypes.c_int() for _ in range(5)]
+    rc = load().fse_sizes(ctx, *[ctypes.byref(x) for x in v])
+    if rc:
+        raise FSEError(rc, "fse_sizes")
+    return tuple(x.value for x in v)
+
+
+class Context:
+    """One FSE-Shooting problem on one GPU (owns an ``fse_ctx``)."""
+
+    def __init__(self, model, d, S, H, rho, S1, newton_tol=1e-10, newton_maxit=20,
+                 precision="fp64", device=-1):
+        self.h = fse_setup(model, d, S, H, rho, S1, newton_tol, newton_maxit, precision, device)
+        self.n_unknowns, self.U, self.N, self.n, self.band = fse_sizes(self.h)
+        self.d = d
+        self.precision = precision
+
+    @classmethod
+    def from_workload(cls, wl, precision="fp64", newton_tol=None, newton_maxit=None, device=-1):
+        return cls(wl.model, wl.d, wl.S, wl.H, wl.rho, wl.S1,
+                   wl.newton_tol if newton_tol is None else newton_tol,
+                   wl.newton_maxit if newton_maxit is None else newton_maxit, precision, device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, allow=()):
+        if rc != FSE_OK and rc not in allow:
+            raise FSEError(rc, fse_last_error(self.h))
+        return rc
+
+    def harmonics(self):
+        out = np.zeros(((self.U + 1) // 2) * (self.d - 1), np.int32)
+        self._check(load().fse_harmonics(self.h, _ip(out)))
+        return out.reshape(-1, self.d - 1)
+
+    def residual_jacobian(self, Z0, omega1, want_jacobian=True, allow_status=(FSE_ENOCONV,)):
+        """fse_residual_jacobian(): returns (R, traj_status, newton_iters, rc)."""
+        Z = np.ascontiguousarray(Z0, dtype=np.float64)
+        assert Z.size == self.n_unknowns
+        R = np.zeros(self.n_unknowns)
+        st = np.zeros(self.N, np.int32)
+        it = np.zeros(self.N, np.int32)
+        rc = load().fse_residual_jacobian(self.h, _dp(Z), float(omega1), _dp(R), int(want_jacobian),
+                                          _ip(st), _ip(it))
+        self._check(rc, allow_status)
+        return R, st, it, rc
+
+    def residual_jacobian_dev(self, Z0_ptr, omega1, R_ptr, want_jacobian=True, stream=0):
+        """fse_residual_jacobian_dev() on device pointers (ints), async on ``stream``."""
+        rc = load().fse_residual_jacobian_dev(self.h, ctypes.c_void_p(Z0_ptr), float(omega1),
+                                              ctypes.c_void_p(R_ptr), int(want_jacobian),
+                                              ctypes.c_void_p(stream))
+        return self._check(rc)
+
+    def status(self):
+        st = np.zeros(self.N, np.int32)
+        it = np.zeros(self.N, np.int32)
+        rc = load().fse_status(self.h, _ip(st), _ip(it))
+        return rc, st, it
+
+    def jacobian_apply(self, V):
+        V = np.ascontiguousarray(np.atleast_2d(V), dtype=np.float64)
+        out = np.zeros_like(V)
+        self._check(load().fse_jacobian_apply(self.h, _dp(V), _dp(out), V.shape[0]))
+        return out
+
+    def jacobian_domega(self):
+        out = np.zeros(self.n_unknowns)
+        self._check(load().fse_jacobian_domega(self.h, _dp(out)))
+        return out
+
+    def jacobian_dense(self):
+        m = self.n_unknowns
+        J = np.zeros((m, m))
+        self._check(load().fse_jacobian_dense(self.h, _dp(J)))
+        return J
+
+    def monodromy(self):
+        Phi = np.zeros((self.N, 2 * self.n, 2 * self.n))
+        dz = np.zeros((self.N, 2 * self.n))
+        self._check(load().fse_monodromy(self.h, _dp(Phi), _dp(dz)))
+        return Phi, dz
+
+    def newton_step(self, Z0, omega1):
+        Z = np.ascontiguousarray(Z0, dtype=np.float64).copy()
+        rn = ctypes.c_double()
+        rc = load().fse_newton_step(self.h, _dp(Z), float(omega1), ctypes.byref(rn))
+        self._check(rc, (FSE_ENOCONV,))
+        return Z, rn.value, rc
+
+    def lyapunov(self, Z0, omega1, N_Ly, h):
+        Z = np.ascontiguousarray(Z0, dtype=np.float64)
+        out = np.zeros(h)
+        rc = load().fse_lyapunov(self.h, _dp(Z), float(omega1), int(N_Ly), int(h), _dp(out))
+        self._check(rc, (FSE_ENOCONV,))
+        return out
+
+    def timings(self):
+        out = np.zeros(5)
+        load().fse_timings(self.h, _dp(out), 5)
+        return out

@@ -1,0 +1,173 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, on the same seeded inputs.
+
+Every call goes through the C ABI (ctypes binding).  Parity runs use a fixed
+per-step Newton count (tol <= 0) on both sides so that both reach the same
+root to rounding.  Tolerances:
+  FP64 sensitivities: residual and monodromy within 1e-10 relative;
+  FP32 sensitivities: residual within 1e-10 (the state path is FP64 in every
+  mode), monodromy within 1e-3 relative (FP32 propagation over S1 steps).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fse_oracle as O
+from paper_2508_06302_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _fse():
+    from paper_2508_06302_gb300 import fse
+    fse.load()
+    return fse
+
+
+CASES = {
+    # name: (model maker, d, S, H, S1, rho, w factor, coefficient scale)
+    "chain6_d2": (lambda: I.chain(6), 2, [7], [3], 24, [I.GOLDEN], 1.15, 5e-3),
+    "beam18_d2": (lambda: I.eb_beam(), 2, [16], [7], 64, [I.GOLDEN], 1.1, 1e-3),
+    "vk87_d2": (lambda: I.vk_beam(n_el=30, F1=1.0, F2=1.0), 2, [5], [2], 48, [I.GOLDEN], 1.1, 1e-6),
+    "shell90_d2": (lambda: I.flat_shell(nx=6, ny=4), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
+    "chain5_d3": (lambda: I.chain(5, F=(1.0, 0.5, 0.3)), 3, [3, 5], [1, 2], 16,
+                  [math.sqrt(2), math.sqrt(3)], 1.1, 1e-3),
+    "chain4_d3_e1": (lambda: I.chain(4, F=(1.0,)), 3, [3, 3], [1, 1], 12, [0.37, 0.71], 1.2, 1e-3),
+}
+
+
+def _setup(name, precision="fp64", maxit=10):
+    mk, d, S, H, S1, rho, wf, sc = CASES[name]
+    m = mk()
+    w1 = wf * m.omega_n1
+    prob = O.FSEProblem(m, S, H, S1, rho)
+    U = O.u_tilde(H)
+    Z = I.random_coeffs(m.n, U, sc, seed=7)
+    # scale the u-coefficients like the q ones (u = dq/dphi_1 is O(q) for the low modes)
+    fse = _fse()
+    ctx = fse.Context(m, d, S, H, rho, S1, newton_tol=0.0, newton_maxit=maxit, precision=precision)
+    return m, prob, ctx, Z, w1
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_monodromy_fp64(name):
+    m, prob, ctx, Z, w1 = _setup(name)
+    ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=10)
+    R, st, it, rc = ctx.residual_jacobian(Z, w1, want_jacobian=True)
+    assert rc == 0 and np.all(st == 0)
+    scale = np.linalg.norm(Z) + np.linalg.norm(ref.R)
+    assert np.linalg.norm(R - ref.R) <= 1e-10 * scale, np.linalg.norm(R - ref.R) / scale
+    Phi, dz = ctx.monodromy()
+    for s in range(prob.N):
+        np.testing.assert_allclose(Phi[s], ref.Phi[s], rtol=0, atol=1e-10 * np.abs(ref.Phi[s]).max())
+        np.testing.assert_allclose(dz[s], ref.dz_dw[s], rtol=0, atol=1e-10 * np.abs(ref.dz_dw[s]).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["beam18_d2", "shell90_d2", "chain5_d3"])
+def test_jacobian_products_fp64(name):
+    m, prob, ctx, Z, w1 = _setup(name)
+    ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=True, tol=0, maxit=10)
+    ctx.residual_jacobian(Z, w1, want_jacobian=True)
+    J = ctx.jacobian_dense()
+    np.testing.assert_allclose(J, ref.J, rtol=0, atol=1e-10 * np.abs(ref.J).max())
+    rng = np.random.default_rng(3)
+    V = rng.standard_normal((2, Z.size))
+    Jv = ctx.jacobian_apply(V)
+    for k in range(2):
+        np.testing.assert_allclose(Jv[k], ref.J @ V[k], rtol=0, atol=1e-10 * np.abs(ref.J @ V[k]).max())
+    dw = ctx.jacobian_domega()
+    np.testing.assert_allclose(dw, ref.dR_dw, rtol=0, atol=1e-10 * np.abs(ref.dR_dw).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "chain5_d3"])
+def test_mixed_fp32(name):
+    m, prob, ctx, Z, w1 = _setup(name, precision="mixed_fp32", maxit=12)
+    ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=10)
+    R, st, it, rc = ctx.residual_jacobian(Z, w1, want_jacobian=True)
+    assert rc == 0
+    scale = np.linalg.norm(Z) + np.linalg.norm(ref.R)
+    assert np.linalg.norm(R - ref.R) <= 1e-10 * scale
+    Phi, dz = ctx.monodromy()
+    err = np.linalg.norm(Phi - ref.Phi) / np.linalg.norm(ref.Phi)
+    assert err < 1e-3, err
+    ctx.close()
+
+
+def test_linear_closed_form_root_on_gpu():
+    """f_nl = 0: the discrete closed-form response is a root of Eq. (16) on the GPU too."""
+    m = I.eb_beam().linear_only()
+    w1 = 1.1 * m.omega_n1
+    S1, H = 128, [7]
+    Dl = 2 * math.pi / S1
+    n = m.n
+    C = np.zeros((2 * n, 15))
+    for lam, F, col in ((1.0, m.F[0], 0), (I.GOLDEN, m.F[1], 1)):
+        s = 2j / Dl * math.tan(lam * Dl / 2)
+        Q = np.linalg.solve(m.K + w1 * s * m.D + w1 ** 2 * s * s * m.M, F)
+        if col == 0:
+            C[:n, 0], C[n:, 0] = Q.real, (s * Q).real
+        else:
+            C[:n, 1], C[n:, 1] = Q.real, (s * Q).real
+            C[:n, 2], C[n:, 2] = -Q.imag, -(s * Q).imag
+    Z = C.reshape(-1)
+    fse = _fse()
+    ctx = fse.Context(m, 2, [16], H, [I.GOLDEN], S1, newton_tol=0, newton_maxit=2)
+    R, st, it, rc = ctx.residual_jacobian(Z, w1, want_jacobian=False)
+    assert np.linalg.norm(R) <= 1e-11 * np.linalg.norm(Z)
+    ctx.close()
+
+
+def test_newton_converges_to_oracle_solution():
+    m = I.eb_beam()
+    w1 = 1.1 * m.omega_n1
+    prob = O.FSEProblem(m, [16], [7], 64, [I.GOLDEN])
+    Zref, hist, ok = O.solve_torus(prob, np.zeros(2 * m.n * 15), w1, rel_tol=1e-12, tol=0, maxit=6)
+    assert ok
+    fse = _fse()
+    ctx = fse.Context(m, 2, [16], [7], [I.GOLDEN], 64, newton_tol=0, newton_maxit=6)
+    Z = np.zeros_like(Zref)
+    norms = []
+    for _ in range(6):
+        Z, rn, rc = ctx.newton_step(Z, w1)
+        norms.append(rn)
+    assert np.linalg.norm(Z - Zref) <= 1e-9 * np.linalg.norm(Zref), norms
+    ctx.close()
+
+
+def test_lyapunov_matches_oracle():
+    m = I.eb_beam()
+    w1 = 1.1 * m.omega_n1
+    prob = O.FSEProblem(m, [16], [7], 64, [I.GOLDEN])
+    Z, _, ok = O.solve_torus(prob, np.zeros(2 * m.n * 15), w1, rel_tol=1e-12, tol=0, maxit=6)
+    ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=6)
+    sig_ref = O.lyapunov(prob, ref.Phi, w1, N_Ly=100, h=8)
+    fse = _fse()
+    ctx = fse.Context(m, 2, [16], [7], [I.GOLDEN], 64, newton_tol=0, newton_maxit=6)
+    sig = ctx.lyapunov(Z, w1, N_Ly=100, h=8)
+    np.testing.assert_allclose(sig, sig_ref, rtol=0, atol=1e-6)
+    ctx.close()
+
+
+def test_newton_status_reported():
+    m = I.eb_beam()
+    fse = _fse()
+    ctx = fse.Context(m, 2, [16], [7], [I.GOLDEN], 32, newton_tol=1e-15, newton_maxit=1)
+    Z = I.random_coeffs(m.n, 15, 1e-3, seed=1)
+    R, st, it, rc = ctx.residual_jacobian(Z, 1.1 * m.omega_n1, want_jacobian=False)
+    assert rc == fse.FSE_ENOCONV and np.all(st == fse.FSE_ENOCONV)
+    ctx.close()
+
+
+def test_setup_rejects_bad_input():
+    fse = _fse()
+    m = I.chain(4)
+    with pytest.raises(fse.FSEError) as ei:
+        fse.Context(m, 2, [6], [3], [0.5], 16)          # S < 2H + 1
+    assert ei.value.code == fse.FSE_EINVAL
+    bad = I.chain(4)
+    bad.M = -bad.M
+    with pytest.raises(fse.FSEError) as ei:
+        fse.Context(bad, 2, [7], [3], [0.5], 16)
+    assert ei.value.code == fse.FSE_ENONPOS_PIVOT
