@@ -96,6 +96,8 @@ typedef struct fse_ctx fse_ctx;
  * On error *out is NULL.  device < 0 uses the current device. */
 int fse_setup(const fse_model* model, const fse_opts* opts, int device, fse_ctx** out);
 
+/* Wait for the context's work, free all its device memory and the handle.
+ * NULL is ignored. */
 void fse_destroy(fse_ctx* ctx);
 
 /* Text of the last error of ctx (or of the last failed fse_setup if ctx is NULL). */
@@ -158,14 +160,29 @@ int fse_newton_step(fse_ctx* ctx, double* Z0, double omega1, double* res_norm_ou
  * (Eq. F3), trigonometric interpolation of Psi over phi~ with the context
  * harmonics at phi~ = 2 (i-1) pi rho, QR re-orthonormalisation for
  * i = 1..N_Ly, sigma_j = sum_i ln|R_i[j,j]| / (N_Ly T_1), j < h.
- * Re-evaluates the Jacobian at Z0 (FP64 sensitivities are used whatever the
- * context precision).  sigma_out: h doubles (host). */
+ * Re-evaluates the Jacobian at Z0 in the context precision (create the
+ * context with FSE_FP64 for the certified exponents).  1 <= h <= min(64, 2n).
+ * sigma_out: h doubles (host). */
 int fse_lyapunov(fse_ctx* ctx, const double* Z0, double omega1, int N_Ly, int h,
                  double* sigma_out);
 
-/* Device time of the phases of the last evaluation, milliseconds:
- * [0] total, [1] per-step state Newton + factorisation, [2] sensitivity
- * right-hand side, [3] sensitivity solves, [4] AFT. Up to `cap` values. */
+/* Integrate only the first n_steps (> 0) Newmark steps of the period in the
+ * following evaluations; 0 restores the full period S1.  With n_steps < S1
+ * the "residual" is the DFT of the truncated trajectories' end states minus
+ * Z0 and the monodromy covers the truncated map: meant for sampled timing and
+ * sampled parity checks of large workloads. */
+int fse_set_steps(fse_ctx* ctx, int n_steps);
+
+/* Enable (1) or disable (0) per-kernel timing: CUDA events are recorded
+ * around every launch of the step loop on the context stream. */
+int fse_profile(fse_ctx* ctx, int enable);
+
+/* Device time of the last evaluation, milliseconds, up to `cap` values:
+ * [0] whole evaluation; with fse_profile on: summed kernel time of
+ * [1] the per-step state Newton + K_eff assembly + banded Cholesky,
+ * [2] the sensitivity right-hand side, [3] the forward and [4] the backward
+ * banded substitutions of the sensitivities (the latter includes the
+ * Newmark update of the tangents).  Waits for the last evaluation. */
 int fse_timings(fse_ctx* ctx, double* ms, int cap);
 
 #ifdef __cplusplus

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libfse_gb300.so"
-SOURCES = ["fse_kernels.cu", "fse_api.cu"]
+SOURCES = ["fse_state.cu", "fse_sens.cu", "fse_aft.cu", "fse_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -33,7 +33,7 @@ def lib_path() -> str:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "fse_internal.h"),
+    deps = [src, os.path.join(CSRC, "fse_internal.h"), os.path.join(CSRC, "fse_common.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "fse.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps if os.path.exists(d))
 

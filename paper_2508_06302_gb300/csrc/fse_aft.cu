@@ -1,0 +1,421 @@
+// AFT (Eq. 20, 21, 15, 16), structured Jacobian products (Eq. 22, 23), the dense
+// outer Newton solve and the Lyapunov exponents (App. F).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "fse_common.cuh"
+
+namespace fse {
+
+// ----------------------------------------------------------------------------
+// AFT: i-DFT (Eq. 20) and DFT + rotation + residual (Eq. 21, 15, 16)
+// ----------------------------------------------------------------------------
+
+__global__ void k_idft(int N, int U, int n2, const double* __restrict__ G,
+                       const double* __restrict__ Z, double* zb) {
+    const int s = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < U; ++c) acc += G[(size_t)s * U + c] * Z[(size_t)i * U + c];
+        zb[(size_t)s * n2 + i] = acc;
+    }
+}
+
+__global__ void k_join(int N, int n, const double* q, const double* u, double* zb) {
+    const size_t total = (size_t)N * n;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = idx / n, i = idx % n;
+        zb[s * 2 * n + i] = q[idx];
+        zb[s * 2 * n + n + i] = u[idx];
+    }
+}
+
+// out[i*U + c] = sum_s RG[c][s] zb[s][i] - (subtract ? Z0[i*U + c] : 0); one warp per output
+__global__ void k_dft_res(int N, int U, int n2, const double* __restrict__ RG,
+                          const double* __restrict__ zb, const double* __restrict__ Z0, double* out,
+                          int subtract) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int total = n2 * U;
+    if (warp >= total) return;
+    const int i = warp / U, c = warp % U;
+    double acc = 0.0;
+    for (int s = lane; s < N; s += 32) acc += RG[(size_t)c * N + s] * zb[(size_t)s * n2 + i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[warp] = acc - (subtract ? Z0[warp] : 0.0);
+}
+
+// ----------------------------------------------------------------------------
+// Jacobian products (Eq. 22, 23) from the stored tangents
+// ----------------------------------------------------------------------------
+
+// zout[s][i] = sum_{j < 2n} Phi_s[i][j] zin[s][j],  Phi_s = [X[:, :2n]; V[:, :2n]]; one warp per (s, i)
+template <typename T>
+__global__ void k_phi_apply(int N, int n, int P, const T* X, const T* V, const double* zin,
+                            double* zout) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int n2 = 2 * n;
+    if (warp >= N * n2) return;
+    const int s = warp / n2, i = warp % n2;
+    const T* row = (i < n ? X + ((size_t)s * n + i) * P : V + ((size_t)s * n + (i - n)) * P);
+    const double* z = zin + (size_t)s * n2;
+    double acc = 0.0;
+    for (int j = lane; j < n2; j += 32) acc += (double)row[j] * z[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) zout[warp] = acc;
+}
+
+template <typename T>
+__global__ void k_domega_col(int N, int n, int P, const T* X, const T* V, double* zout) {
+    const int n2 = 2 * n;
+    const size_t total = (size_t)N * n2;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = idx / n2;
+        const int i = (int)(idx % n2);
+        const T* row = (i < n ? X + (s * n + i) * P : V + (s * n + (i - n)) * P);
+        zout[idx] = (double)row[2 * n];
+    }
+}
+
+template <typename T>
+__global__ void k_phi_copy(int N, int n, int P, const T* X, const T* V, double* Phi, double* dzdw) {
+    const int n2 = 2 * n;
+    const size_t total = (size_t)N * n2 * n2;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = idx / ((size_t)n2 * n2);
+        const int r = (int)((idx / n2) % n2), c = (int)(idx % n2);
+        const T* row = (r < n ? X + (s * n + r) * P : V + (s * n + (r - n)) * P);
+        if (Phi) Phi[idx] = (double)row[c];
+        if (dzdw && c == 0) dzdw[s * n2 + r] = (double)row[2 * n];
+    }
+}
+
+// dense Eq. (22): J[(i,u),(j,v)] = sum_s RG[u][s] Phi_s[i][j] G[s][v] - delta
+template <typename T>
+__global__ void k_dense_jac(int N, int n, int U, int P, const T* X, const T* V,
+                            const double* RG, const double* G, double* J) {
+    const int n2 = 2 * n;
+    const size_t m = (size_t)n2 * U;
+    const size_t total = m * m;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = idx / m, col = idx % m;
+        const int i = (int)(row / U), uu = (int)(row % U);
+        const int j = (int)(col / U), vv = (int)(col % U);
+        double acc = 0.0;
+        for (int s = 0; s < N; ++s) {
+            const T* xr = (i < n ? X + ((size_t)s * n + i) * P : V + ((size_t)s * n + (i - n)) * P);
+            acc += RG[(size_t)uu * N + s] * (double)xr[j] * G[(size_t)s * U + vv];
+        }
+        J[idx] = acc - (row == col ? 1.0 : 0.0);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// dense LU with partial pivoting (FP64) for the outer Newton step
+// ----------------------------------------------------------------------------
+
+__global__ void k_lu_pivot(double* A, double* bvec, int* piv, int m, int k, int* flag) {
+    __shared__ double sv[1024];
+    __shared__ int si[1024];
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+        const double v = fabs(A[(size_t)i * m + k]);
+        if (v > best) {
+            best = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double v2 = sv[threadIdx.x + o];
+            const int i2 = si[threadIdx.x + o];
+            if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    const int p = si[0];
+    if (threadIdx.x == 0) {
+        piv[k] = p;
+        if (!(sv[0] > 0.0)) *flag = 1;
+    }
+    if (p != k) {
+        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+            const double t = A[(size_t)k * m + c];
+            A[(size_t)k * m + c] = A[(size_t)p * m + c];
+            A[(size_t)p * m + c] = t;
+        }
+        if (threadIdx.x == 0) {
+            const double t = bvec[k];
+            bvec[k] = bvec[p];
+            bvec[p] = t;
+        }
+    }
+}
+
+__global__ void k_lu_update(double* A, double* bvec, int m, int k) {
+    const double pv = A[(size_t)k * m + k];
+    const int rows = m - k - 1;
+    const size_t total = (size_t)rows * (m - k);
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = k + 1 + (int)(idx / (m - k));
+        const int c = k + (int)(idx % (m - k));
+        const double l = A[(size_t)i * m + k] / pv;
+        if (c == k) {
+            // the multiplier is written after all reads of column k by this row are done
+            continue;
+        }
+        A[(size_t)i * m + c] -= l * A[(size_t)k * m + c];
+        if (c == k + 1) bvec[i] -= l * bvec[k];
+    }
+}
+
+__global__ void k_lu_mult(double* A, int m, int k) {
+    const double pv = A[(size_t)k * m + k];
+    for (int i = k + 1 + blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        A[(size_t)i * m + k] /= pv;
+}
+
+__global__ void k_back_subst(const double* A, double* x, int m) {
+    // single block, sequential over rows, parallel dot products
+    __shared__ double red[1024];
+    for (int i = m - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) acc += A[(size_t)i * m + c] * x[c];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) x[i] = (x[i] - red[0]) / A[(size_t)i * m + i];
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Lyapunov exponents (App. F)
+// ----------------------------------------------------------------------------
+
+// weights w_s(phi) = sum_c H_c(phi) Gamma^-1[c][s] of the trigonometric interpolant
+__global__ void k_lyap_weights(int N, int U, int dm1, const int* ktab, const double* Gi,
+                               double phi0, double phi1, double phi2, double* wts) {
+    const double ph[3] = {phi0, phi1, phi2};
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        double acc = Gi[s];
+        for (int c = 1; c < U; ++c) {
+            const int l = (c - 1) >> 1;
+            double arg = 0.0;
+            for (int j = 0; j < dm1; ++j) arg += (double)ktab[l * dm1 + j] * ph[j];
+            const double h = ((c - 1) & 1) ? sin(arg) : cos(arg);
+            acc += h * Gi[(size_t)c * N + s];
+        }
+        wts[s] = acc;
+    }
+}
+
+// A[i][c] = sum_s w_s sum_j Psi_s[i][j] Q[j][c],  Psi = diag(1, w) Phi diag(1, 1/w)  (Eq. F3)
+template <typename T>
+__global__ void k_lyap_prop(int N, int n, int P, int h, double w, const T* X, const T* V,
+                            const double* wts, const double* Q, double* Aout) {
+    const int n2 = 2 * n;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n2 * h) return;
+    const int i = warp / h, c = warp % h;
+    const double si = (i < n) ? 1.0 : w;
+    double acc = 0.0;
+    for (int s = 0; s < N; ++s) {
+        const T* row = (i < n ? X + ((size_t)s * n + i) * P : V + ((size_t)s * n + (i - n)) * P);
+        double a2 = 0.0;
+        for (int j = lane; j < n2; j += 32) {
+            const double sj = (j < n) ? 1.0 : 1.0 / w;
+            a2 += (double)row[j] * sj * Q[(size_t)j * h + c];
+        }
+        acc += wts[s] * a2;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) Aout[(size_t)i * h + c] = si * acc;
+}
+
+// classical Gram-Schmidt with re-orthogonalisation, one CTA: Q R = A; acc[c] += ln R[c][c]
+__global__ void k_lyap_qr(int m, int h, double* A, double* Q, double* acc) {
+    __shared__ double red[1024];
+    __shared__ double coef[64];
+    for (int c = 0; c < h; ++c) {
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < c; ++k) {
+                double d = 0.0;
+                for (int i = threadIdx.x; i < m; i += blockDim.x) d += Q[(size_t)i * h + k] * A[(size_t)i * h + c];
+                red[threadIdx.x] = d;
+                __syncthreads();
+                for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) coef[k] = red[0];
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                double v = A[(size_t)i * h + c];
+                for (int k = 0; k < c; ++k) v -= coef[k] * Q[(size_t)i * h + k];
+                A[(size_t)i * h + c] = v;
+            }
+            __syncthreads();
+        }
+        double d = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) d += A[(size_t)i * h + c] * A[(size_t)i * h + c];
+        red[threadIdx.x] = d;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        const double nrm = sqrt(red[0]);
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) Q[(size_t)i * h + c] = A[(size_t)i * h + c] / nrm;
+        if (threadIdx.x == 0) acc[c] += log(nrm);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+
+void launch_idft(fse_ctx* c, const double* Z, double* zb) {
+    const Params& p = c->p;
+    dim3 g((2 * p.n + 127) / 128, p.N);
+    k_idft<<<g, 128, 0, c->stream>>>(p.N, p.U, 2 * p.n, c->d.G, Z, zb);
+}
+
+void launch_collect_end(fse_ctx* c) {
+    const Params& p = c->p;
+    const size_t tot = (size_t)p.N * p.n;
+    k_join<<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, c->d.q, c->d.u, c->d.zb);
+}
+
+void launch_dft_residual(fse_ctx* c, const double* zb, const double* Z0, double* R, int subtract) {
+    const Params& p = c->p;
+    const size_t warps = (size_t)2 * p.n * p.U;
+    k_dft_res<<<(int)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(p.N, p.U, 2 * p.n, c->d.RG, zb,
+                                                                      Z0, R, subtract);
+}
+
+void launch_phi_apply(fse_ctx* c, const double* zin, double* zout) {
+    const Params& p = c->p;
+    const size_t warps = (size_t)p.N * 2 * p.n;
+    const int g = (int)((warps * 32 + 255) / 256);
+    if (p.prec == FSE_MIXED_FP32)
+        k_phi_apply<float><<<g, 256, 0, c->stream>>>(p.N, p.n, p.ld, (const float*)c->d.X,
+                                                    (const float*)c->d.V, zin, zout);
+    else
+        k_phi_apply<double><<<g, 256, 0, c->stream>>>(p.N, p.n, p.ld, (const double*)c->d.X,
+                                                     (const double*)c->d.V, zin, zout);
+}
+
+void launch_domega(fse_ctx* c, double* zout) {
+    const Params& p = c->p;
+    const size_t tot = (size_t)p.N * 2 * p.n;
+    if (p.prec == FSE_MIXED_FP32)
+        k_domega_col<float><<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, p.ld, (const float*)c->d.X,
+                                                                  (const float*)c->d.V, zout);
+    else
+        k_domega_col<double><<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, p.ld, (const double*)c->d.X,
+                                                                   (const double*)c->d.V, zout);
+}
+
+void launch_phi_copy(fse_ctx* c, double* Phi, double* dzdw) {
+    const Params& p = c->p;
+    const size_t tot = (size_t)p.N * 4 * p.n * p.n;
+    if (p.prec == FSE_MIXED_FP32)
+        k_phi_copy<float><<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, p.ld, (const float*)c->d.X,
+                                                                (const float*)c->d.V, Phi, dzdw);
+    else
+        k_phi_copy<double><<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, p.ld, (const double*)c->d.X,
+                                                                 (const double*)c->d.V, Phi, dzdw);
+}
+
+void launch_dense_jac(fse_ctx* c, double* J) {
+    const Params& p = c->p;
+    const size_t m = (size_t)2 * p.n * p.U;
+    if (p.prec == FSE_MIXED_FP32)
+        k_dense_jac<float><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, J);
+    else
+        k_dense_jac<double><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, J);
+}
+
+int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m) {
+    int* flag = nullptr;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return FSE_ENOMEM;
+    cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+    for (int k = 0; k < m; ++k) {
+        k_lu_pivot<<<1, 1024, 0, c->stream>>>(A, bvec, c->piv, m, k, flag);
+        if (k + 1 < m) {
+            const size_t tot = (size_t)(m - k - 1) * (m - k);
+            k_lu_update<<<nblocks(tot, 256, 152 * 32), 256, 0, c->stream>>>(A, bvec, m, k);
+            k_lu_mult<<<nblocks(m - k - 1, 256), 256, 0, c->stream>>>(A, m, k);
+        }
+    }
+    k_back_subst<<<1, 1024, 0, c->stream>>>(A, bvec, m);
+    int h = 0;
+    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(flag);
+    return h ? FSE_ENONPOS_PIVOT : FSE_OK;
+}
+
+int lyapunov_run(fse_ctx* c, double w, int N_Ly, int h, double* sigma) {
+    const Params& p = c->p;
+    const int m = 2 * p.n;
+    double *Q = nullptr, *A = nullptr, *acc = nullptr, *wts = nullptr;
+    if (cudaMalloc(&Q, sizeof(double) * m * h) != cudaSuccess) return FSE_ENOMEM;
+    cudaMalloc(&A, sizeof(double) * m * h);
+    cudaMalloc(&acc, sizeof(double) * h);
+    cudaMalloc(&wts, sizeof(double) * p.N);
+    std::vector<double> Q0((size_t)m * h, 0.0);
+    for (int c2 = 0; c2 < h; ++c2) Q0[(size_t)c2 * h + c2] = 1.0;
+    cudaMemcpyAsync(Q, Q0.data(), sizeof(double) * m * h, cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(acc, 0, sizeof(double) * h, c->stream);
+    const size_t warps = (size_t)m * h;
+    const int g = (int)((warps * 32 + 255) / 256);
+    for (int i = 1; i <= N_Ly; ++i) {
+        double ph[3] = {0, 0, 0};
+        for (int j = 0; j < p.d - 1; ++j) ph[j] = 2.0 * (i - 1) * M_PI * c->rho[j];
+        k_lyap_weights<<<nblocks(p.N, 128), 128, 0, c->stream>>>(p.N, p.U, p.d - 1, c->d.ktab, c->d.Gi,
+                                                             ph[0], ph[1], ph[2], wts);
+        if (p.prec == FSE_MIXED_FP32)
+            k_lyap_prop<float><<<g, 256, 0, c->stream>>>(p.N, p.n, p.ld, h, w, (const float*)c->d.X,
+                                                        (const float*)c->d.V, wts, Q, A);
+        else
+            k_lyap_prop<double><<<g, 256, 0, c->stream>>>(p.N, p.n, p.ld, h, w, (const double*)c->d.X,
+                                                         (const double*)c->d.V, wts, Q, A);
+        k_lyap_qr<<<1, 512, 0, c->stream>>>(m, h, A, Q, acc);
+    }
+    std::vector<double> hacc(h);
+    cudaMemcpyAsync(hacc.data(), acc, sizeof(double) * h, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaFree(Q);
+    cudaFree(A);
+    cudaFree(acc);
+    cudaFree(wts);
+    if (e != cudaSuccess) return FSE_ECUDA;
+    const double T1 = 2.0 * M_PI / w;
+    for (int j = 0; j < h; ++j) sigma[j] = hacc[j] / (N_Ly * T1);
+    return FSE_OK;
+}
+
+}  // namespace fse

@@ -66,17 +66,22 @@ static cudaError_t dalloc(P** p, size_t bytes) {
 
 static void free_ctx(fse_ctx* c) {
     if (!c) return;
-    void* ptrs[] = {c->d.Mb, c->d.Db, c->d.Kb, c->d.Sb, c->d.F, c->d.el_type, c->d.el_dof, c->d.el_p,
-                    c->d.col_off, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs, c->d.ktab,
-                    c->d.LMc, c->d.LMr, c->d.LMinv, c->d.LMc_t, c->d.LMr_t, c->d.LMinv_t, c->d.q,
-                    c->d.u, c->d.a, c->d.zb, c->d.Kt0, c->d.Lc, c->d.Lr, c->d.Linv, c->d.X, c->d.V,
-                    c->d.W, c->d.Y, c->d.Z0, c->d.R, c->d.vec, c->d.vec2, c->d.yb, c->d.status,
-                    c->d.iters, c->Jd, c->piv};
+    void* ptrs[] = {c->d.Mb, c->d.F, c->d.el_type, c->d.el_dof, c->d.el_p, c->d.col_off,
+                    c->d.cs_ptr, c->d.cs_col, c->d.cs_slot, c->d.kt_slot, c->d.cs_m, c->d.cs_d, c->d.cs_k, c->d.cs_s, c->d.cs_A,
+                    c->d.cs_B, c->d.kt_ptr, c->d.kt_col, c->d.kt_soff, c->d.kt_src, c->d.ke,
+                    c->d.kt_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
+                    c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
+                    c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
+                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->Jd, c->piv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto* v : {&c->pev, &c->ev_state, &c->ev_sens})
+        for (auto& e : *v)
+            if (e) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
     delete c;
 }
 
@@ -143,12 +148,6 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.n_el = m->n_nl;
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
     const int nb = b + 1;
-    p.smem_state = (size_t)6 * n * sizeof(double) + (size_t)nb * nb * tsz;
-    if (p.smem_state > 200 * 1024 || (size_t)nb * 128 * tsz > 200 * 1024 ||
-        (size_t)nb * nb * sizeof(double) > 200 * 1024) {
-        free_ctx(c);
-        return set_err(nullptr, FSE_EINVAL, "n or half-bandwidth too large for the on-chip working set");
-    }
     for (int j = 0; j < o->d - 1; ++j) c->rho.push_back(o->rho[j]);
     if (device >= 0) {
         if (cudaSetDevice(device) != cudaSuccess) {
@@ -160,12 +159,13 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         cudaGetDevice(&c->device);
     }
     int rc = cuda_check(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+    if (rc == FSE_OK) rc = cuda_check(c, cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking), "stream");
     if (rc) {
         g_setup_err = c->err;
         free_ctx(c);
         return rc;
     }
-    for (auto& e : c->ev) cudaEventCreate(&e);
+    for (auto& e : c->ev) cudaEventCreateWithFlags(&e, cudaEventDefault);
     // harmonic table
     auto rows = harmonic_rows(H);
     const int dm1 = p.d - 1;
@@ -191,17 +191,25 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         rcv[l] = cos(th);
         rsv[l] = sin(th);
     }
-    // diagonal-major full bands
+    // diagonal-major full band of M (for its factor) and the CSR of the union pattern of M, D, K
     const int fb = 2 * b + 1;
-    std::vector<double> Mb((size_t)fb * n, 0.0), Db((size_t)fb * n, 0.0), Kb((size_t)fb * n, 0.0);
-    for (int i = 0; i < n; ++i)
-        for (int cc = 0; cc < fb; ++cc) {
-            const int j = i + cc - b;
-            if (j < 0 || j >= n) continue;
-            Mb[(size_t)cc * n + i] = m->M[(size_t)i * n + j];
-            Db[(size_t)cc * n + i] = m->D[(size_t)i * n + j];
-            Kb[(size_t)cc * n + i] = m->K[(size_t)i * n + j];
+    std::vector<double> Mb((size_t)fb * n, 0.0);
+    std::vector<int> cptr(n + 1, 0), ccol;
+    std::vector<double> cm, cd, ck;
+    for (int i = 0; i < n; ++i) {
+        for (int j = std::max(0, i - b); j <= std::min(n - 1, i + b); ++j) {
+            const size_t o2 = (size_t)i * n + j;
+            Mb[(size_t)(j - i + b) * n + i] = m->M[o2];
+            if (m->M[o2] != 0.0 || m->D[o2] != 0.0 || m->K[o2] != 0.0) {
+                ccol.push_back(j);
+                cm.push_back(m->M[o2]);
+                cd.push_back(m->D[o2]);
+                ck.push_back(m->K[o2]);
+            }
         }
+        cptr[i + 1] = (int)ccol.size();
+    }
+    p.nnz = (int)ccol.size();
     // colour the elements so that no two of a colour share a dof
     std::vector<int> color(m->n_nl, 0);
     std::vector<uint64_t> used(n, 0);
@@ -239,22 +247,83 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         coff[color[order[k]] + 1]++;
     }
     for (int cl = 0; cl < ncol; ++cl) coff[cl + 1] += coff[cl];
+    // CSR pattern of K_t: entry (dof_a, dof_b) for every element and local pair; each entry
+    // keeps its sources (element in sorted order, a, b) in increasing element order
+    std::vector<std::vector<std::pair<int, int>>> ktrow(n);   // (col, source)
+    for (int k = 0; k < m->n_nl; ++k) {
+        const int nd = et[k] == 1 ? 1 : (et[k] == 2 ? 2 : 6);
+        for (int a = 0; a < nd; ++a)
+            for (int bb = 0; bb < nd; ++bb) {
+                const int ga = ed[(size_t)6 * k + a], gb = ed[(size_t)6 * k + bb];
+                if (ga >= 0 && gb >= 0) ktrow[ga].push_back({gb, k * 36 + a * 6 + bb});
+            }
+    }
+    std::vector<int> kptr(n + 1, 0), kcol, ksoff(1, 0), ksrc;
+    for (int i = 0; i < n; ++i) {
+        auto& r = ktrow[i];
+        std::stable_sort(r.begin(), r.end(), [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+            return x.first < y.first;
+        });
+        for (size_t q = 0; q < r.size(); ++q) {
+            if (q == 0 || r[q].first != r[q - 1].first) {
+                kcol.push_back(r[q].first);
+                ksoff.push_back(ksoff.back());
+            }
+            ksrc.push_back(r[q].second);
+            ksoff.back()++;
+        }
+        kptr[i + 1] = (int)kcol.size();
+    }
+    p.nnz_kt = (int)kcol.size();
+    p.nblk = (n + FSE_BLK - 1) / FSE_BLK;
+    p.ld = (p.P + 3) & ~3;
+    p.RW = 2 * b + 8;
+    p.RWT = 1;
+    while (p.RWT < b + FSE_BLK) p.RWT <<= 1;
+    std::vector<int> cslot(ccol.size()), kslot(kcol.size());
+    for (size_t q = 0; q < ccol.size(); ++q) cslot[q] = ccol[q] % p.RW;
+    for (size_t q = 0; q < kcol.size(); ++q) kslot[q] = kcol[q] % p.RW;
+    p.smem_state = fse::state_smem(p);
+    p.smem_rhs = fse::rhs_smem(p);
+    p.smem_trsm = fse::trsm_smem(p);
+    const size_t lim = 220 * 1024;
+    if (p.smem_state > lim || p.smem_rhs > lim || p.smem_trsm > lim ||
+        (size_t)nb * nb * sizeof(double) + (size_t)(b * nb / 2 + 2) * 4 > lim) {
+        free_ctx(c);
+        return set_err(nullptr, FSE_EINVAL, "n or half-bandwidth too large for the on-chip working set");
+    }
     // device allocations
     const size_t Nn = (size_t)N * n, band = (size_t)fb * n, lb = (size_t)n * nb;
-    const size_t sensz = (size_t)N * n * p.P * tsz;
+    const size_t sensz = (size_t)N * n * p.ld * tsz;
+    const size_t ktsz = (size_t)N * std::max(1, p.nnz_kt) * tsz;
+    const size_t dsz = (size_t)N * p.nblk * FSE_BLK * FSE_BLK * tsz;
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** ptr, size_t bytes) {
         if (e == cudaSuccess) e = dalloc(ptr, bytes);
     };
     A(&c->d.Mb, band * 8);
-    A(&c->d.Db, band * 8);
-    A(&c->d.Kb, band * 8);
-    A(&c->d.Sb, band * 8);
     A(&c->d.F, (size_t)m->e * n * 8);
     A(&c->d.el_type, (size_t)std::max(1, m->n_nl) * 4);
     A(&c->d.el_dof, (size_t)std::max(1, m->n_nl) * 24);
     A(&c->d.el_p, (size_t)std::max(1, m->n_nl) * 48);
     A(&c->d.col_off, (size_t)(ncol + 1) * 4);
+    A(&c->d.cs_ptr, (size_t)(n + 1) * 4);
+    A(&c->d.cs_col, (size_t)p.nnz * 4);
+    A(&c->d.cs_slot, (size_t)p.nnz * 4);
+    A(&c->d.kt_slot, (size_t)std::max(1, p.nnz_kt) * 4);
+    A(&c->d.cs_m, (size_t)p.nnz * 8);
+    A(&c->d.cs_d, (size_t)p.nnz * 8);
+    A(&c->d.cs_k, (size_t)p.nnz * 8);
+    A(&c->d.cs_s, (size_t)p.nnz * 8);
+    A(&c->d.cs_A, (size_t)p.nnz * tsz);
+    A(&c->d.cs_B, (size_t)p.nnz * tsz);
+    A(&c->d.kt_ptr, (size_t)(n + 1) * 4);
+    A(&c->d.kt_col, (size_t)std::max(1, p.nnz_kt) * 4);
+    A(&c->d.kt_soff, (size_t)(p.nnz_kt + 1) * 4);
+    A(&c->d.kt_src, (size_t)std::max<size_t>(1, ksrc.size()) * 4);
+    A(&c->d.ke, (size_t)N * std::max(1, m->n_nl) * 36 * 8);
+    A(&c->d.kt_val, FSE_NBUF_KT * ktsz);
+    A(&c->d.romega, (size_t)2 * Nn * tsz);
     A(&c->d.phis, (size_t)N * dm1 * 8);
     A(&c->d.G, (size_t)N * U * 8);
     A(&c->d.Gi, (size_t)N * U * 8);
@@ -265,23 +334,17 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     A(&c->d.LMc, lb * 8);
     A(&c->d.LMr, lb * 8);
     A(&c->d.LMinv, (size_t)n * 8);
-    if (p.prec == FSE_MIXED_FP32) {
-        A(&c->d.LMc_t, lb * 4);
-        A(&c->d.LMr_t, lb * 4);
-        A(&c->d.LMinv_t, (size_t)n * 4);
-    }
     A(&c->d.q, Nn * 8);
     A(&c->d.u, Nn * 8);
     A(&c->d.a, Nn * 8);
     A(&c->d.zb, Nn * 16);
     A(&c->d.yb, Nn * 16);
-    A(&c->d.Kt0, (size_t)N * lb * 8);
-    A(&c->d.Lc, (size_t)N * lb * tsz);
-    A(&c->d.Lr, (size_t)N * lb * tsz);
-    A(&c->d.Linv, Nn * tsz);
+    A(&c->d.Lc, FSE_NBUF_F * (size_t)N * lb * tsz);
+    A(&c->d.Lr, FSE_NBUF_F * (size_t)N * lb * tsz);
+    A(&c->d.Linv, FSE_NBUF_F * Nn * tsz);
+    A(&c->d.Dinv, FSE_NBUF_F * dsz);
     A(&c->d.X, sensz);
     A(&c->d.V, sensz);
-    A(&c->d.W, sensz);
     A(&c->d.Y, sensz);
     const size_t nu = (size_t)2 * n * U;
     A(&c->d.Z0, nu * 8);
@@ -298,8 +361,6 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     }
     cudaStream_t st = c->stream;
     cudaMemcpyAsync(c->d.Mb, Mb.data(), band * 8, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->d.Db, Db.data(), band * 8, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->d.Kb, Kb.data(), band * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.F, m->F, (size_t)m->e * n * 8, cudaMemcpyHostToDevice, st);
     if (m->n_nl > 0) {
         cudaMemcpyAsync(c->d.el_type, et.data(), et.size() * 4, cudaMemcpyHostToDevice, st);
@@ -307,6 +368,19 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         cudaMemcpyAsync(c->d.el_p, ep.data(), ep.size() * 8, cudaMemcpyHostToDevice, st);
     }
     cudaMemcpyAsync(c->d.col_off, coff.data(), coff.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.cs_ptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.cs_col, ccol.data(), ccol.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.cs_slot, cslot.data(), cslot.size() * 4, cudaMemcpyHostToDevice, st);
+    if (p.nnz_kt > 0) cudaMemcpyAsync(c->d.kt_slot, kslot.data(), kslot.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.cs_m, cm.data(), cm.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.cs_d, cd.data(), cd.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.cs_k, ck.data(), ck.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.kt_ptr, kptr.data(), kptr.size() * 4, cudaMemcpyHostToDevice, st);
+    if (p.nnz_kt > 0) {
+        cudaMemcpyAsync(c->d.kt_col, kcol.data(), kcol.size() * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d.kt_src, ksrc.data(), ksrc.size() * 4, cudaMemcpyHostToDevice, st);
+    }
+    cudaMemcpyAsync(c->d.kt_soff, ksoff.data(), ksoff.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.phis, phis.data(), phis.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.rc, rcv.data(), rcv.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.rs, rsv.data(), rsv.size() * 8, cudaMemcpyHostToDevice, st);
@@ -360,23 +434,58 @@ static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, i
     cudaSetDevice(c->device);
     const Params& p = c->p;
     if (w != c->omega_S) {
-        fse::launch_build_S(c, w);
+        fse::launch_build_ops(c, w);
         c->omega_S = w;
     }
-    cudaEventRecord(c->ev[0], c->stream);
-    fse::launch_idft(c, Z0_dev, c->d.zb, 1);
-    fse::launch_init_state(c, w, sens);
-    if (sens) fse::launch_sens_init(c, w);
-    for (int k = 0; k < p.S1; ++k) {
-        fse::launch_state_step(c, k, w, sens);
-        if (sens) {
-            fse::launch_sens_step(c, w, 0);
-            fse::launch_sens_step(c, w, 1);
+    const int steps = (c->n_steps > 0 && c->n_steps < p.S1) ? c->n_steps : p.S1;
+    if ((int)c->ev_state.size() < steps) {
+        for (int k = (int)c->ev_state.size(); k < steps; ++k) {
+            cudaEvent_t a = nullptr, b2 = nullptr;
+            cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&b2, cudaEventDisableTiming);
+            c->ev_state.push_back(a);
+            c->ev_sens.push_back(b2);
         }
     }
+    const bool prof = c->prof && (int)c->pev.size() == 8 * p.S1;
+    auto rec = [&](int phase, int k, int end, cudaStream_t st) {
+        if (prof) cudaEventRecord(c->pev[((size_t)phase * p.S1 + k) * 2 + end], st);
+    };
+    cudaStream_t s1 = c->stream, s2 = c->stream2;
+    cudaEventRecord(c->ev[0], s1);
+    fse::launch_idft(c, Z0_dev, c->d.zb);
+    fse::launch_init_state(c, w);
+    if (sens) {
+        cudaEventRecord(c->ev[2], s1);
+        cudaStreamWaitEvent(s2, c->ev[2], 0);
+        fse::launch_sens_init(c, s2);
+    }
+    // state step k (stream 1) writes the factor and w_1-term buffers k % 2 and the tangent
+    // values (k + 1) % 3, which the sensitivity step k - 2 (stream 2) reads: it waits for it.
+    // The sensitivity step k waits for the state step k; so state k + 1 overlaps sensitivity k.
+    for (int k = 0; k < steps; ++k) {
+        if (sens && k >= 2) cudaStreamWaitEvent(s1, c->ev_sens[k - 2], 0);
+        rec(0, k, 0, s1);
+        fse::launch_state_step(c, k, w, s1);
+        rec(0, k, 1, s1);
+        if (sens) {
+            cudaEventRecord(c->ev_state[k], s1);
+            cudaStreamWaitEvent(s2, c->ev_state[k], 0);
+            for (int ph = 0; ph < 3; ++ph) {
+                rec(1 + ph, k, 0, s2);
+                fse::launch_sens_phase(c, k, w, ph, s2);
+                rec(1 + ph, k, 1, s2);
+            }
+            cudaEventRecord(c->ev_sens[k], s2);
+        }
+    }
+    c->prof_pending = prof;
+    c->prof_sens = sens != 0;
+    c->prof_steps = steps;
     fse::launch_collect_end(c);
     fse::launch_dft_residual(c, c->d.zb, Z0_dev, R_dev, 1);
-    cudaEventRecord(c->ev[1], c->stream);
+    if (sens) cudaStreamWaitEvent(s1, c->ev_sens[steps - 1], 0);
+    cudaEventRecord(c->ev[1], s1);
     c->have_jac = sens != 0;
     c->omega_jac = w;
     return cuda_check(c, cudaGetLastError(), "evaluation launch");
@@ -391,6 +500,21 @@ static int collect_status(fse_ctx* c, int* ts, int* it) {
     if (rc) return rc;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) c->timing[0] = ms;
+    if (c->prof_pending) {
+        const int S1 = c->p.S1;
+        const int steps = c->prof_steps;
+        for (int ph = 0; ph < 4; ++ph) {
+            double tot = 0.0;
+            if (ph == 0 || c->prof_sens)
+                for (int k = 0; k < steps; ++k) {
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, c->pev[((size_t)ph * S1 + k) * 2], c->pev[((size_t)ph * S1 + k) * 2 + 1]);
+                    tot += t;
+                }
+            c->timing[1 + ph] = tot;
+        }
+        c->prof_pending = false;
+    }
     if (ts) std::memcpy(ts, st.data(), N * 4);
     if (it) std::memcpy(it, its.data(), N * 4);
     int worst = FSE_OK;
@@ -443,7 +567,7 @@ extern "C" int fse_jacobian_apply(fse_ctx* c, const double* v, double* Jv, int n
     const size_t nu = (size_t)2 * c->p.n * c->p.U;
     for (int k = 0; k < nvec; ++k) {
         cudaMemcpyAsync(c->d.vec, v + k * nu, nu * 8, cudaMemcpyHostToDevice, c->stream);
-        fse::launch_idft(c, c->d.vec, c->d.zb, 1);
+        fse::launch_idft(c, c->d.vec, c->d.zb);
         fse::launch_phi_apply(c, c->d.zb, c->d.yb);
         fse::launch_dft_residual(c, c->d.yb, c->d.vec, c->d.vec2, 1);
         cudaMemcpyAsync(Jv + k * nu, c->d.vec2, nu * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -553,6 +677,26 @@ extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, in
     if (st < 0 && st != FSE_ENOCONV) return st;
     rc = fse::lyapunov_run(c, w, N_Ly, h, sigma);
     return rc ? rc : st;
+}
+
+extern "C" int fse_set_steps(fse_ctx* c, int n_steps) {
+    if (!c || n_steps < 0) return FSE_EINVAL;
+    c->n_steps = n_steps;
+    return FSE_OK;
+}
+
+extern "C" int fse_profile(fse_ctx* c, int enable) {
+    if (!c) return FSE_EINVAL;
+    cudaSetDevice(c->device);
+    c->prof = enable != 0;
+    if (c->prof && (int)c->pev.size() != 8 * c->p.S1) {
+        for (auto& e : c->pev)
+            if (e) cudaEventDestroy(e);
+        c->pev.assign((size_t)8 * c->p.S1, nullptr);
+        for (auto& e : c->pev)
+            if (cudaEventCreate(&e) != cudaSuccess) return set_err(c, FSE_ECUDA, "event creation failed");
+    }
+    return FSE_OK;
 }
 
 extern "C" int fse_timings(fse_ctx* c, double* ms, int cap) {

@@ -9,29 +9,52 @@
 #include "../../include/fse.h"
 
 #define FSE_MAX_D 4
+#define FSE_BLK 32        // row block of the blocked triangular solves
+#define FSE_NBUF_F 2      // factor buffers (step parity)
+#define FSE_NBUF_KT 3     // tangent-value buffers (step index mod 3)
 
 namespace fse {
 
-// Banded storage used by every kernel (b = half-bandwidth, detected at setup):
-//  full band  A[i*(2b+1) + (j - i + b)],  |j - i| <= b      (M, D, K, S in FP64)
-//  col band   C[j*(b+1) + (i - j)],      j <= i <= j + b    (lower factor, by columns)
-//  row band   R[i*(b+1) + (j - i + b)],  i - b <= j <= i    (lower factor, by rows)
-// Entries outside [0, n) are stored as exact zeros.
-// Sensitivities of trajectory s: X[s][i][t], i < n dofs, t < P = 2n + 1 tangent
-// directions (dz0 for t < 2n, d w_1 for t = 2n), row-major so that consecutive t
-// are contiguous.
+// Storage used by the kernels (b = half-bandwidth, detected at setup):
+//  * M, D, K, S and the sensitivity operators are CSR on the union of the
+//    exact nonzero patterns of M, D, K (sorted columns, shared by all
+//    trajectories); the M factor of setup uses the diagonal-major full band
+//    A[c*n + i] = A(i, i+c-b).
+//  * K_t(q) of the nonlinear elements is CSR on its own pattern; its values
+//    are per trajectory, summed from per-element tangents in a fixed order.
+//  * factor of K_eff, per trajectory: column band Lc[j*(b+1) + (i-j)], row band
+//    Lr[i*(b+1) + (j-i+b)], 1/L_jj, and the inverses of the 32x32 diagonal
+//    blocks Dinv[B][r][c] (lower triangular, identity padding past n).
+//  * tangents of trajectory s: X[s][i][t], V[s][i][t], i < n, t < P = 2n+1
+//    (d/dz0 for t < 2n, d/dw_1 for t = 2n), consecutive t contiguous.
 
 struct Dev {
-    // model
-    double* Mb = nullptr;    // n x (2b+1)
-    double* Db = nullptr;
-    double* Kb = nullptr;
-    double* Sb = nullptr;    // effective stiffness S of Eq. (E7), rebuilt per w_1
+    // model (FP64)
+    double* Mb = nullptr;    // full band of M (setup factor)
     double* F = nullptr;     // e x n
-    int* el_type = nullptr;  // elements sorted by colour
+    int* el_type = nullptr;  // nonlinear elements sorted by colour
     int* el_dof = nullptr;   // 6 per element
     double* el_p = nullptr;  // 6 per element
     int* col_off = nullptr;  // ncolors + 1
+    // CSR of the union pattern of M, D, K
+    int* cs_ptr = nullptr;
+    int* cs_col = nullptr;
+    int* cs_slot = nullptr;  // cs_col mod RW (ring slot of the right-hand-side kernel)
+    double* cs_m = nullptr;
+    double* cs_d = nullptr;
+    double* cs_k = nullptr;
+    double* cs_s = nullptr;  // S of Eq. (E7) for the current w_1 (FP64)
+    void* cs_A = nullptr;    // w^2 4/D^2 M + w 2/D D - K (sensitivity precision)
+    void* cs_B = nullptr;    // w^2 4/D M
+    // CSR of the K_t pattern and the element-tangent sources of each entry
+    int* kt_ptr = nullptr;
+    int* kt_col = nullptr;
+    int* kt_slot = nullptr;  // kt_col mod RW
+    int* kt_soff = nullptr;
+    int* kt_src = nullptr;   // element * 36 + a * 6 + b
+    double* ke = nullptr;    // N x n_el x 36 element tangents (scratch of k_state)
+    void* kt_val = nullptr;  // FSE_NBUF_KT x N x nnz_kt
+    void* romega = nullptr;  // 2 x N x n   right-hand side of the w_1 column
     // AFT tables
     double* phis = nullptr;  // N x (d-1)
     double* G = nullptr;     // N x U   (Eq. D2)
@@ -40,27 +63,23 @@ struct Dev {
     double* rc = nullptr;    // L rotation cos
     double* rs = nullptr;    // L rotation sin
     int* ktab = nullptr;     // L x (d-1)
-    // factor of M (FP64) and its copy in the sensitivity precision
+    // factor of M (FP64)
     double* LMc = nullptr;
     double* LMr = nullptr;
     double* LMinv = nullptr;
-    void* LMc_t = nullptr;
-    void* LMr_t = nullptr;
-    void* LMinv_t = nullptr;
     // trajectory state (FP64)
     double* q = nullptr;     // N x n
     double* u = nullptr;
     double* a = nullptr;
     double* zb = nullptr;    // N x 2n  (start / end points)
-    double* Kt0 = nullptr;   // N x n x (b+1) col band of K_t(q_0)
-    // per-trajectory factor of K_eff (sensitivity precision)
-    void* Lc = nullptr;      // N x n x (b+1)
-    void* Lr = nullptr;      // N x n x (b+1)
-    void* Linv = nullptr;    // N x n
-    // sensitivities (sensitivity precision)
-    void* X = nullptr;       // N x n x P
+    // factor of K_eff (sensitivity precision), FSE_NBUF_F buffers
+    void* Lc = nullptr;      // NBUF x N x n x (b+1)
+    void* Lr = nullptr;
+    void* Linv = nullptr;    // NBUF x N x n
+    void* Dinv = nullptr;    // NBUF x N x nblk x 32 x 32
+    // tangents (sensitivity precision)
+    void* X = nullptr;       // N x n x ld (columns P..ld-1 are zero padding)
     void* V = nullptr;
-    void* W = nullptr;
     void* Y = nullptr;       // right-hand side / forward-substitution buffer
     // vectors
     double* Z0 = nullptr;    // 2nU
@@ -74,9 +93,12 @@ struct Dev {
 
 struct Params {
     int n = 0, b = 0, d = 0, e = 0, N = 0, U = 0, L = 0, S1 = 0, P = 0;
-    int maxit = 0, prec = 0, ncolors = 0, n_el = 0;
+    int maxit = 0, prec = 0, ncolors = 0, n_el = 0, nnz = 0, nnz_kt = 0, nblk = 0;
+    int ld = 0;              // row stride of the tangent arrays: P rounded up to a multiple of 4
+    int RW = 0;              // ring rows of the right-hand-side kernel (2b + 8)
+    int RWT = 0;             // ring rows of the blocked solves (power of two >= b + 32)
     double tol = 0;
-    size_t smem_state = 0;
+    size_t smem_state = 0, smem_rhs = 0, smem_trsm = 0;
 };
 
 }  // namespace fse
@@ -85,16 +107,24 @@ struct fse_ctx {
     fse::Params p;
     fse::Dev d;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // state path + everything ordered
+    cudaStream_t stream2 = nullptr;  // sensitivity kernels (overlap with the next state step)
     std::string err;
     std::vector<int> ktab_host;
     std::vector<double> rho;
-    double omega_S = -1.0;       // w_1 the effective stiffness was built for
+    double omega_S = -1.0;       // w_1 the operators were built for
     bool have_jac = false;
-    bool jac_fp64 = false;
     double omega_jac = 0.0;
     cudaEvent_t ev[8] = {};
+    std::vector<cudaEvent_t> ev_state, ev_sens;   // per-step ordering events
     double timing[5] = {0, 0, 0, 0, 0};
+    // optional per-kernel timing: events around every launch of the step loop
+    bool prof = false;
+    int n_steps = 0;                // 0 = the whole period
+    std::vector<cudaEvent_t> pev;   // [phase][k][begin/end], phase 0 state, 1 rhs, 2 fwd, 3 bwd
+    bool prof_pending = false;
+    bool prof_sens = false;
+    int prof_steps = 0;
     // scratch for the dense Newton solve
     double* Jd = nullptr;
     int* piv = nullptr;
@@ -103,15 +133,21 @@ struct fse_ctx {
 
 namespace fse {
 
-// launchers (fse_kernels.cu)
+// dynamic shared memory of the state, right-hand-side and blocked-solve kernels
+size_t state_smem(const Params& p);
+size_t rhs_smem(const Params& p);
+size_t trsm_smem(const Params& p);
+
+// launchers
+void ensure_constants();
 void launch_fill_tables(fse_ctx* c);
-void launch_build_S(fse_ctx* c, double omega1);
+void launch_build_ops(fse_ctx* c, double omega1);
 int launch_factor_M(fse_ctx* c);
-void launch_idft(fse_ctx* c, const double* Z, double* zb, int nvec);
-void launch_init_state(fse_ctx* c, double omega1, int want_sens);
-void launch_state_step(fse_ctx* c, int k, double omega1, int want_sens);
-void launch_sens_init(fse_ctx* c, double omega1);
-void launch_sens_step(fse_ctx* c, double omega1, int phase);
+void launch_idft(fse_ctx* c, const double* Z, double* zb);
+void launch_init_state(fse_ctx* c, double omega1);
+void launch_state_step(fse_ctx* c, int k, double omega1, cudaStream_t st);
+void launch_sens_init(fse_ctx* c, cudaStream_t st);
+void launch_sens_phase(fse_ctx* c, int k, double omega1, int phase, cudaStream_t st);
 void launch_collect_end(fse_ctx* c);
 void launch_dft_residual(fse_ctx* c, const double* zb, const double* Z0, double* R, int subtract);
 void launch_phi_apply(fse_ctx* c, const double* zin, double* zout);

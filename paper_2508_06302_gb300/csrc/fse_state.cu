@@ -1,0 +1,663 @@
+// Trajectory state path of FSE-Shooting (App. E): one CTA per trajectory per
+// Newmark step; FP64 state, residual and Newton test; factor of the effective
+// stiffness in the sensitivity precision T.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "fse_common.cuh"
+
+namespace fse {
+
+static bool g_const_ready = false;
+
+void ensure_constants() {
+    if (g_const_ready) return;
+    // closed forms of the 5-point Gauss-Legendre rule
+    const double r = 2.0 * sqrt(10.0 / 7.0);
+    double x[5] = {-sqrt(5.0 + r) / 3.0, -sqrt(5.0 - r) / 3.0, 0.0, sqrt(5.0 - r) / 3.0,
+                   sqrt(5.0 + r) / 3.0};
+    const double s70 = 13.0 * sqrt(70.0);
+    double w[5] = {(322.0 - s70) / 900.0, (322.0 + s70) / 900.0, 128.0 / 225.0,
+                   (322.0 + s70) / 900.0, (322.0 - s70) / 900.0};
+    cudaMemcpyToSymbol(c_glx, x, sizeof(x));
+    cudaMemcpyToSymbol(c_glw, w, sizeof(w));
+    g_const_ready = true;
+}
+
+// ----------------------------------------------------------------------------
+// AFT tables (App. D, Eq. 14) and per-w_1 operators
+// ----------------------------------------------------------------------------
+
+__global__ void k_tables(int N, int U, int dm1, const int* __restrict__ ktab,
+                         const double* __restrict__ phis, const double* __restrict__ rc,
+                         const double* __restrict__ rs, double* G, double* Gi, double* RG) {
+    const int s = blockIdx.x;
+    for (int c = threadIdx.x; c < U; c += blockDim.x) {
+        double g;
+        if (c == 0) {
+            g = 1.0;
+        } else {
+            const int l = (c - 1) >> 1;
+            double arg = 0.0;
+            for (int j = 0; j < dm1; ++j) arg += (double)ktab[l * dm1 + j] * phis[s * dm1 + j];
+            g = ((c - 1) & 1) ? sin(arg) : cos(arg);
+        }
+        G[(size_t)s * U + c] = g;
+        Gi[(size_t)c * N + s] = (c == 0 ? 1.0 : 2.0) * g / (double)N;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < U; c += blockDim.x) {
+        double v;
+        if (c == 0) {
+            v = Gi[s];
+        } else {
+            const int l = (c - 1) >> 1;
+            const double gc = Gi[(size_t)(1 + 2 * l) * N + s], gs = Gi[(size_t)(2 + 2 * l) * N + s];
+            v = ((c - 1) & 1) ? (rs[l] * gc + rc[l] * gs) : (rc[l] * gc - rs[l] * gs);
+        }
+        RG[(size_t)c * N + s] = v;
+    }
+}
+
+// S = w^2 4/D^2 M + w 2/D D + K (Eq. E7) in FP64, and the two operators of the
+// sensitivity right-hand side A = w^2 4/D^2 M + w 2/D D - K and B = w^2 4/D M.
+template <typename T>
+__global__ void k_build_ops(int nnz, double cm, double cd, double cb, const double* m,
+                            const double* d, const double* k, double* S, T* Aop, T* Bop) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
+        S[e] = cm * m[e] + cd * d[e] + k[e];
+        Aop[e] = T(cm * m[e] + cd * d[e] - k[e]);
+        Bop[e] = T(cb * m[e]);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// banded Cholesky inside one CTA: column band Ac (global, in place) -> Lc, Lr, Linv
+// ----------------------------------------------------------------------------
+
+// pairs (cc, rr), cc in [1, b], rr in [0, b - cc]: entries of the trailing triangle
+__device__ void fill_tri_table(int b, unsigned* tab) {
+    for (int cc = 1; cc <= b; ++cc) {
+        const int base = (cc - 1) * (2 * b - cc + 2) / 2;   // sum_{c'<cc} (b - c' + 1)
+        for (int rr = threadIdx.x; rr <= b - cc; rr += blockDim.x)
+            tab[base + rr] = ((unsigned)cc << 16) | (unsigned)rr;
+    }
+}
+
+template <typename T>
+__device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab) {
+    const int nb = b + 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntri = b * (b + 1) / 2;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    for (int idx = tid; idx < nb * nb; idx += nt) {
+        const int c = idx / nb;
+        wnd[idx] = (c < n) ? Ac[(size_t)c * nb + (idx - c * nb)] : T(0);
+    }
+    __syncthreads();
+    int slot = 0;   // window slot of column j (= j mod nb)
+    for (int j = 0; j < n; ++j, slot = (slot + 1 == nb) ? 0 : slot + 1) {
+        T* colj = wnd + slot * nb;
+        const T piv = colj[0];
+        if (!(piv > T(0)) || !isfinite((double)piv)) {
+            if (tid == 0) bad = 1;
+            __syncthreads();
+            break;
+        }
+        const T ljj = sqrt(piv);
+        const T inv = T(1) / ljj;
+        const T inv2 = inv * inv;
+        // trailing update with the unscaled column: A_ik -= A_ij A_kj / A_jj
+        const int ccmax = n - 1 - j;
+        for (int idx = tid; idx < ntri; idx += nt) {
+            const unsigned pr = tab[idx];
+            const int cc = (int)(pr >> 16), rr = (int)(pr & 0xffffu);
+            if (cc <= ccmax) {
+                int sc = slot + cc;
+                sc = (sc >= nb) ? sc - nb : sc;
+                wnd[sc * nb + rr] -= colj[cc + rr] * colj[cc] * inv2;
+            }
+        }
+        __syncthreads();
+        // write column j of L out and load column j + nb into its slot (each thread owns
+        // the same entries r in both parts, so no barrier is needed between them)
+        const int jn = j + nb;
+        for (int r = tid; r < nb; r += nt) {
+            const T v = (j + r < n) ? (r == 0 ? ljj : colj[r] * inv) : T(0);
+            Ac[(size_t)j * nb + r] = v;
+            if (j + r < n) Lr[(size_t)(j + r) * nb + (b - r)] = v;
+            if (r == 0) {
+                Linv[j] = inv;
+                for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
+            }
+            colj[r] = (jn < n) ? Ac[(size_t)jn * nb + r] : T(0);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    return bad;
+}
+
+// inverses of the 32 x 32 diagonal blocks of L (one warp per block, one lane per column)
+template <typename T>
+__device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int nblk, T* Dinv) {
+    const int nb = b + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int B = warp; B < nblk; B += nw) {
+        const int i0 = B * FSE_BLK;
+        T z[FSE_BLK];
+#pragma unroll
+        for (int i = 0; i < FSE_BLK; ++i) {
+            const int gi = i0 + i;
+            T acc = (i == lane) ? T(1) : T(0);
+            if (gi < n) {
+#pragma unroll
+                for (int j = 0; j < i; ++j) {
+                    const int c = (i0 + j) - gi + b;   // row-band index of L(gi, i0 + j)
+                    if (c >= 0) acc -= Lr[(size_t)gi * nb + c] * z[j];
+                }
+                acc *= Linv[gi];
+            }
+            z[i] = acc;
+        }
+        T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK;
+#pragma unroll
+        for (int i = 0; i < FSE_BLK; ++i) D[i * FSE_BLK + lane] = z[i];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// the state kernel
+// ----------------------------------------------------------------------------
+
+struct StateArgs {
+    int n, b, e, dm1, maxit, ncolors, n_el, nnz_kt, nblk, init;
+    double tol, Dl, a0c, a1c, a2c, w, phi;
+    double rho[FSE_MAX_D - 1];
+    const double *F, *phis;
+    const int *cs_ptr, *cs_col;
+    const double *cs_m, *cs_d, *cs_k, *cs_s;
+    const int *el_type, *el_dof, *col_off;
+    const double* el_p;
+    const int *kt_ptr, *kt_col, *kt_soff, *kt_src;
+    double* ke;
+    void* kt_out;       // N x nnz_kt, K_t at the new state
+    void* romega;       // N x n, w_1-column term of this step (regular steps)
+    const double *LMc, *LMr, *LMinv;
+    double *q, *u, *a;
+    const void *cLc, *cLr, *cLinv, *cDinv;   // chord factor (regular steps)
+    void *oLc, *oLr, *oLinv, *oDinv;         // factor of K_eff at the new state
+    int *status, *iters;
+};
+
+__device__ __forceinline__ double forcing_i(const StateArgs& A, int s, int i, double phi) {
+    double e = A.F[i] * cos(phi);
+    for (int j = 1; j < A.e; ++j)
+        e += A.F[(size_t)j * A.n + i] * cos(A.phis[s * A.dm1 + (j - 1)] + A.rho[j - 1] * phi);
+    return e;
+}
+
+// r += f_nl(q), elements processed colour by colour (no two elements of a colour share a dof)
+__device__ void add_fnl(const StateArgs& A, const double* q, double* r) {
+    for (int c = 0; c < A.ncolors; ++c) {
+        const int e0 = A.col_off[c], e1 = A.col_off[c + 1];
+        for (int el = e0 + threadIdx.x; el < e1; el += blockDim.x) {
+            const int type = A.el_type[el];
+            const int* dof = A.el_dof + 6 * el;
+            double fe[6];
+            elem_eval(type, dof, A.el_p + 6 * el, q, fe, nullptr);
+            const int nd = elem_ndof(type);
+            for (int a = 0; a < nd; ++a)
+                if (dof[a] >= 0) r[dof[a]] += fe[a];
+        }
+        __syncthreads();
+    }
+}
+
+// Ac = lower column band of S + K_t(q) (type T), kt_out = K_t(q) values on its CSR pattern.
+template <typename T>
+__device__ void assemble_keff(const StateArgs& A, int s, const double* q, T* Ac, T* kt_out) {
+    const int n = A.n, b = A.b, nb = b + 1;
+    double* ke = A.ke + (size_t)s * A.n_el * 36;
+    for (int el = threadIdx.x; el < A.n_el; el += blockDim.x) {
+        double fe[6];
+        elem_eval(A.el_type[el], A.el_dof + 6 * el, A.el_p + 6 * el, q, fe, ke + (size_t)el * 36);
+    }
+    for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) Ac[idx] = T(0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int e1 = A.cs_ptr[i + 1];
+        for (int e = A.cs_ptr[i]; e < e1; ++e) {
+            const int j = A.cs_col[e];
+            if (j <= i) Ac[(size_t)j * nb + (i - j)] = T(A.cs_s[e]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int e1 = A.kt_ptr[i + 1];
+        for (int e = A.kt_ptr[i]; e < e1; ++e) {
+            double v = 0.0;
+            const int s1 = A.kt_soff[e + 1];
+            for (int k = A.kt_soff[e]; k < s1; ++k) v += ke[A.kt_src[k]];
+            kt_out[e] = T(v);
+            const int j = A.kt_col[e];
+            if (j <= i) {
+                const size_t o = (size_t)j * nb + (i - j);
+                Ac[o] = T((double)Ac[o] + v);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Blocked banded solve L L^T x = r in place (r in shared memory, FP64 arithmetic,
+// factor of type T): 32-row blocks, off-diagonal band part as dot products,
+// diagonal blocks through their stored inverses.
+template <typename T>
+__device__ void cta_blocked_solve(const T* __restrict__ Lc, const T* __restrict__ Lr,
+                                  const T* __restrict__ Dinv, int n, int b, int nblk, double* r,
+                                  double* tmp) {
+    const int nb = b + 1;
+    const int row = threadIdx.x >> 3, l8 = threadIdx.x & 7;   // 32 rows x 8 lanes
+    // forward: y_B = Dinv_B (r_B - L_{B,<} y_<)
+    for (int B = 0; B < nblk; ++B) {
+        const int i0 = B * FSE_BLK, i = i0 + row;
+        double part = 0.0;
+        if (i < n && row < FSE_BLK) {
+            for (int c = l8; c < b; c += 8) {
+                const int j = i0 - b + c;        // column left of the block
+                const int bi = c - row;          // row-band index of L(i, j)
+                if (j >= 0 && bi >= 0) part += (double)Lr[(size_t)i * nb + bi] * r[j];
+            }
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        if (l8 == 0 && row < FSE_BLK) tmp[row] = (i < n) ? r[i] - part : 0.0;
+        __syncthreads();
+        double y = 0.0;
+        if (row < FSE_BLK) {
+            const T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK + row * FSE_BLK;
+            for (int k = l8; k <= row; k += 8) y += (double)D[k] * tmp[k];
+        }
+        y += __shfl_xor_sync(0xffffffffu, y, 4);
+        y += __shfl_xor_sync(0xffffffffu, y, 2);
+        y += __shfl_xor_sync(0xffffffffu, y, 1);
+        if (l8 == 0 && row < FSE_BLK && i < n) r[i] = y;
+        __syncthreads();
+    }
+    // backward: x_B = Dinv_B^T (y_B - L_{>,B}^T x_>)
+    for (int B = nblk - 1; B >= 0; --B) {
+        const int i0 = B * FSE_BLK, i = i0 + row;
+        double part = 0.0;
+        if (i < n && row < FSE_BLK) {
+            for (int c = l8; c < b; c += 8) {
+                const int k = i0 + FSE_BLK + c;  // row below the block
+                const int ci = k - i;            // column-band index of L(k, i)
+                if (k < n && ci <= b) part += (double)Lc[(size_t)i * nb + ci] * r[k];
+            }
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        if (l8 == 0 && row < FSE_BLK) tmp[row] = (i < n) ? r[i] - part : 0.0;
+        __syncthreads();
+        double x = 0.0;
+        if (row < FSE_BLK) {
+            const T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK;
+            for (int k = row + l8; k < FSE_BLK; k += 8) x += (double)D[k * FSE_BLK + row] * tmp[k];
+        }
+        x += __shfl_xor_sync(0xffffffffu, x, 4);
+        x += __shfl_xor_sync(0xffffffffu, x, 2);
+        x += __shfl_xor_sync(0xffffffffu, x, 1);
+        if (l8 == 0 && row < FSE_BLK && i < n) r[i] = x;
+        __syncthreads();
+    }
+}
+
+// Single-warp banded solve of the FP64 mass factor (setup-time layouts), used once per
+// evaluation for the consistent initial acceleration.
+__device__ void warp_band_solve_fp64(const double* __restrict__ Lc, const double* __restrict__ Lr,
+                                     const double* __restrict__ Linv, int n, int b, double* r) {
+    const int lane = threadIdx.x & 31;
+    const int nb = b + 1;
+    for (int j = 0; j < n; ++j) {
+        const double x = r[j] * Linv[j];
+        __syncwarp();
+        if (lane == 0) r[j] = x;
+        for (int rr = 1 + lane; rr <= b; rr += 32) {
+            const int i = j + rr;
+            if (i < n) r[i] -= Lc[(size_t)j * nb + rr] * x;
+        }
+        __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        const double x = r[j] * Linv[j];
+        __syncwarp();
+        if (lane == 0) r[j] = x;
+        for (int rr = 1 + lane; rr <= b; rr += 32) {
+            const int i = j - rr;
+            if (i >= 0) r[i] -= Lr[(size_t)j * nb + b - rr] * x;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_state(StateArgs A) {
+    const int s = blockIdx.x, n = A.n, b = A.b, nb = b + 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    extern __shared__ double sm[];
+    double *sq = sm, *su = sq + n, *sa = su + n, *sqn = sa + n, *sb = sqn + n, *sr = sb + n;
+    double* tmp = sr + n;                                 // 32
+    unsigned* tab = reinterpret_cast<unsigned*>(tmp + FSE_BLK);
+    const int ntri = b * (b + 1) / 2;
+    T* wnd = reinterpret_cast<T*>(tab + ((ntri + 1) & ~1));
+    __shared__ int s_conv, s_stat;
+    const size_t off = (size_t)s * n;
+    const size_t foff = (size_t)s * n * nb;
+    const size_t doff = (size_t)s * A.nblk * FSE_BLK * FSE_BLK;
+    T* oLc = reinterpret_cast<T*>(A.oLc) + foff;
+    T* oLr = reinterpret_cast<T*>(A.oLr) + foff;
+    T* oLi = reinterpret_cast<T*>(A.oLinv) + off;
+    T* oDi = reinterpret_cast<T*>(A.oDinv) + doff;
+    T* kt_out = reinterpret_cast<T*>(A.kt_out) + (size_t)s * A.nnz_kt;
+    fill_tri_table(b, tab);
+    if (tid == 0) {
+        s_stat = A.init ? 0 : A.status[s];
+        s_conv = 0;
+    }
+    for (int i = tid; i < n; i += nt) {
+        sq[i] = A.q[off + i];
+        su[i] = A.u[off + i];
+        if (!A.init) sa[i] = A.a[off + i];
+    }
+    __syncthreads();
+    int it = 0;
+    if (A.init) {
+        // consistent start: w^2 M a0 = e(0) - w D u0 - K q0 - f_nl(q0)  (Eq. E2 at phi_1 = 0)
+        for (int i = tid; i < n; i += nt) sr[i] = 0.0;
+        __syncthreads();
+        add_fnl(A, sq, sr);
+        for (int i = tid; i < n; i += nt)
+            sb[i] = forcing_i(A, s, i, 0.0) - A.w * csr_row(A.cs_ptr, A.cs_col, A.cs_d, i, su) -
+                    csr_row(A.cs_ptr, A.cs_col, A.cs_k, i, sq) - sr[i];
+        __syncthreads();
+        if (tid < 32) warp_band_solve_fp64(A.LMc, A.LMr, A.LMinv, n, b, sb);
+        __syncthreads();
+        const double iw2 = 1.0 / (A.w * A.w);
+        for (int i = tid; i < n; i += nt) {
+            sa[i] = sb[i] * iw2;
+            A.a[off + i] = sa[i];
+        }
+        __syncthreads();
+    } else {
+        const T* cLc = reinterpret_cast<const T*>(A.cLc) + foff;
+        const T* cLr = reinterpret_cast<const T*>(A.cLr) + foff;
+        const T* cDi = reinterpret_cast<const T*>(A.cDinv) + doff;
+        // b = e_{k+1} + w^2 M (a0 q + a1 u + a) + w D (a2 q + u)   (Eq. E7)
+        for (int i = tid; i < n; i += nt) {
+            sr[i] = A.a0c * sq[i] + A.a1c * su[i] + sa[i];
+            sqn[i] = A.a2c * sq[i] + su[i];
+        }
+        __syncthreads();
+        const double w2 = A.w * A.w;
+        for (int i = tid; i < n; i += nt)
+            sb[i] = forcing_i(A, s, i, A.phi) + w2 * csr_row(A.cs_ptr, A.cs_col, A.cs_m, i, sr) +
+                    A.w * csr_row(A.cs_ptr, A.cs_col, A.cs_d, i, sqn);
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) sqn[i] = sq[i];   // predictor: the previous displacement
+        __syncthreads();
+        // Newton on Eq. (E6): starts as a chord iteration with the factor of K_eff(q_k) and
+        // refactors at the current iterate whenever the contraction ratio exceeds 0.1
+        double prev = -1.0;
+        for (it = 0; it < A.maxit; ++it) {
+            for (int i = tid; i < n; i += nt) sr[i] = csr_row(A.cs_ptr, A.cs_col, A.cs_s, i, sqn) - sb[i];
+            __syncthreads();
+            add_fnl(A, sqn, sr);
+            cta_blocked_solve<T>(cLc, cLr, cDi, n, b, A.nblk, sr, tmp);
+            double dmax = 0.0, qmax = 0.0;
+            for (int i = tid; i < n; i += nt) {
+                const double v = sqn[i] - sr[i];
+                sqn[i] = v;
+                dmax = fmax(dmax, fabs(sr[i]));
+                qmax = fmax(qmax, fabs(v));
+            }
+            block_max2(dmax, qmax);
+            if (!isfinite(dmax) || !isfinite(qmax)) {
+                if (tid == 0) s_stat = FSE_ENAN;
+                break;
+            }
+            if (A.tol > 0.0 && dmax <= A.tol * qmax) {
+                if (tid == 0) s_conv = 1;
+                ++it;
+                break;
+            }
+            if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit) {
+                assemble_keff<T>(A, s, sqn, oLc, kt_out);
+                if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab)) {
+                    if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
+                    ++it;
+                    break;
+                }
+                cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi);
+                __syncthreads();
+                cLc = oLc;
+                cLr = oLr;
+                cDi = oDi;
+            }
+            prev = dmax;
+        }
+        __syncthreads();
+        if (tid == 0 && A.tol > 0.0 && !s_conv && s_stat == 0) s_stat = FSE_ENOCONV;
+        // corrector (Eq. E5); sums of old and new u, a for the w_1 column of the tangents
+        for (int i = tid; i < n; i += nt) {
+            const double dq = sqn[i] - sq[i];
+            const double un = A.a2c * dq - su[i];
+            const double an = A.a0c * dq - A.a1c * su[i] - sa[i];
+            sb[i] = su[i] + un;
+            sr[i] = sa[i] + an;
+            sq[i] = sqn[i];
+            su[i] = un;
+            sa[i] = an;
+            A.q[off + i] = sqn[i];
+            A.u[off + i] = un;
+            A.a[off + i] = an;
+        }
+        __syncthreads();
+        // w_1 column: -2 w M (a_k + a_{k+1}) - D (u_k + u_{k+1})
+        T* rom = reinterpret_cast<T*>(A.romega) + off;
+        for (int i = tid; i < n; i += nt)
+            rom[i] = T(-2.0 * A.w * csr_row(A.cs_ptr, A.cs_col, A.cs_m, i, sr) -
+                       csr_row(A.cs_ptr, A.cs_col, A.cs_d, i, sb));
+        __syncthreads();
+    }
+    // effective stiffness at the new state, its banded Cholesky factor and block inverses
+    assemble_keff<T>(A, s, sq, oLc, kt_out);
+    const int bad = cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab);
+    if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi);
+    if (tid == 0) {
+        if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
+        A.status[s] = s_stat;
+        A.iters[s] = (A.init ? 0 : A.iters[s]) + it;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// mass factor at setup
+// ----------------------------------------------------------------------------
+
+__global__ void k_factor_M(int n, int b, const double* Mb, double* LMc, double* LMr, double* LMinv,
+                           int* flag) {
+    extern __shared__ double wndM[];
+    const int nb = b + 1;
+    unsigned* tab = reinterpret_cast<unsigned*>(wndM + nb * nb);
+    fill_tri_table(b, tab);
+    for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) {
+        const int j = idx / nb, r = idx - j * nb, i = j + r;
+        LMc[idx] = (i < n) ? Mb[(size_t)(b - r) * n + i] : 0.0;
+    }
+    __syncthreads();
+    const int bad = cta_band_cholesky<double>(LMc, LMr, LMinv, n, b, wndM, tab);
+    if (threadIdx.x == 0) *flag = bad;
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+
+void launch_fill_tables(fse_ctx* c) {
+    ensure_constants();
+    const Params& p = c->p;
+    k_tables<<<p.N, 128, 0, c->stream>>>(p.N, p.U, p.d - 1, c->d.ktab, c->d.phis, c->d.rc, c->d.rs,
+                                         c->d.G, c->d.Gi, c->d.RG);
+}
+
+void launch_build_ops(fse_ctx* c, double w) {
+    const Params& p = c->p;
+    const double Dl = 2.0 * M_PI / p.S1;
+    const double cm = w * w * 4.0 / (Dl * Dl), cd = w * 2.0 / Dl, cb = w * w * 4.0 / Dl;
+    const int g = nblocks(p.nnz, 256);
+    if (p.prec == FSE_MIXED_FP32)
+        k_build_ops<float><<<g, 256, 0, c->stream>>>(p.nnz, cm, cd, cb, c->d.cs_m, c->d.cs_d, c->d.cs_k,
+                                                     c->d.cs_s, (float*)c->d.cs_A, (float*)c->d.cs_B);
+    else
+        k_build_ops<double><<<g, 256, 0, c->stream>>>(p.nnz, cm, cd, cb, c->d.cs_m, c->d.cs_d, c->d.cs_k,
+                                                      c->d.cs_s, (double*)c->d.cs_A, (double*)c->d.cs_B);
+}
+
+int launch_factor_M(fse_ctx* c) {
+    ensure_constants();
+    const Params& p = c->p;
+    const int nb = p.b + 1;
+    int* flag = nullptr;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
+    const size_t smem = (size_t)nb * nb * sizeof(double) + (size_t)(p.b * nb / 2 + 2) * 4;
+    cudaFuncSetAttribute(k_factor_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_factor_M<<<1, 256, smem, c->stream>>>(p.n, p.b, c->d.Mb, c->d.LMc, c->d.LMr, c->d.LMinv, flag);
+    int h = 0;
+    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(flag);
+    return h;
+}
+
+size_t state_smem(const Params& p) {
+    const int nb = p.b + 1;
+    const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
+    const size_t ntri = (size_t)p.b * nb / 2;
+    return (size_t)(6 * p.n + FSE_BLK) * 8 + ((ntri + 1) & ~(size_t)1) * 4 + (size_t)nb * nb * tsz;
+}
+
+static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
+    const Params& p = c->p;
+    const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
+    StateArgs A;
+    A.n = p.n;
+    A.b = p.b;
+    A.e = p.e;
+    A.dm1 = p.d - 1;
+    A.maxit = p.maxit;
+    A.ncolors = p.ncolors;
+    A.n_el = p.n_el;
+    A.nnz_kt = p.nnz_kt;
+    A.nblk = p.nblk;
+    A.init = init;
+    A.tol = p.tol;
+    A.Dl = 2.0 * M_PI / p.S1;
+    A.a0c = 4.0 / (A.Dl * A.Dl);
+    A.a1c = 4.0 / A.Dl;
+    A.a2c = 2.0 / A.Dl;
+    A.w = w;
+    A.phi = (k + 1) * A.Dl;
+    for (int j = 0; j < FSE_MAX_D - 1; ++j) A.rho[j] = j < (int)c->rho.size() ? c->rho[j] : 0.0;
+    A.F = c->d.F;
+    A.phis = c->d.phis;
+    A.cs_ptr = c->d.cs_ptr;
+    A.cs_col = c->d.cs_col;
+    A.cs_m = c->d.cs_m;
+    A.cs_d = c->d.cs_d;
+    A.cs_k = c->d.cs_k;
+    A.cs_s = c->d.cs_s;
+    A.el_type = c->d.el_type;
+    A.el_dof = c->d.el_dof;
+    A.col_off = c->d.col_off;
+    A.el_p = c->d.el_p;
+    A.kt_ptr = c->d.kt_ptr;
+    A.kt_col = c->d.kt_col;
+    A.kt_soff = c->d.kt_soff;
+    A.kt_src = c->d.kt_src;
+    A.ke = c->d.ke;
+    const size_t ktsz = (size_t)p.N * p.nnz_kt * tsz;
+    const size_t fsz = (size_t)p.N * p.n * (p.b + 1) * tsz;
+    const size_t vsz = (size_t)p.N * p.n * tsz;
+    const size_t dsz = (size_t)p.N * p.nblk * FSE_BLK * FSE_BLK * tsz;
+    // state k (new state q_{k+1}) writes K_t(q_{k+1}) to buffer (k+1) % 3 and the factor to k % 2;
+    // the init call (k = -1) writes buffer 0 and factor 1
+    const int kt_idx = (k + 1) % FSE_NBUF_KT;
+    const int fo = ((k % 2) + 2) % 2, fi = 1 - fo;
+    A.kt_out = (char*)c->d.kt_val + kt_idx * ktsz;
+    A.romega = (char*)c->d.romega + (size_t)fo * vsz;
+    A.LMc = c->d.LMc;
+    A.LMr = c->d.LMr;
+    A.LMinv = c->d.LMinv;
+    A.q = c->d.q;
+    A.u = c->d.u;
+    A.a = c->d.a;
+    A.cLc = (char*)c->d.Lc + fi * fsz;
+    A.cLr = (char*)c->d.Lr + fi * fsz;
+    A.cLinv = (char*)c->d.Linv + fi * vsz;
+    A.cDinv = (char*)c->d.Dinv + fi * dsz;
+    A.oLc = (char*)c->d.Lc + fo * fsz;
+    A.oLr = (char*)c->d.Lr + fo * fsz;
+    A.oLinv = (char*)c->d.Linv + fo * vsz;
+    A.oDinv = (char*)c->d.Dinv + fo * dsz;
+    A.status = c->d.status;
+    A.iters = c->d.iters;
+    return A;
+}
+
+template <typename T>
+static void state_launch(fse_ctx* c, const StateArgs& A, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_state<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr_set = true;
+    }
+    k_state<T><<<c->p.N, 256, c->p.smem_state, st>>>(A);
+}
+
+__global__ void k_split(int N, int n, const double* zb, double* q, double* u) {
+    const size_t total = (size_t)N * n;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = idx / n, i = idx % n;
+        q[idx] = zb[s * 2 * n + i];
+        u[idx] = zb[s * 2 * n + n + i];
+    }
+}
+
+void launch_init_state(fse_ctx* c, double w) {
+    ensure_constants();
+    const Params& p = c->p;
+    const size_t tot = (size_t)p.N * p.n;
+    k_split<<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, c->d.zb, c->d.q, c->d.u);
+    StateArgs A = make_state_args(c, w, 1, -1);
+    if (p.prec == FSE_MIXED_FP32)
+        state_launch<float>(c, A, c->stream);
+    else
+        state_launch<double>(c, A, c->stream);
+}
+
+void launch_state_step(fse_ctx* c, int k, double w, cudaStream_t st) {
+    StateArgs A = make_state_args(c, w, 0, k);
+    if (c->p.prec == FSE_MIXED_FP32)
+        state_launch<float>(c, A, st);
+    else
+        state_launch<double>(c, A, st);
+}
+
+}  // namespace fse

@@ -88,6 +88,8 @@ def load(path: Optional[str] = None):
         "fse_newton_step": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP]),
         "fse_lyapunov": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
         "fse_timings": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
+        "fse_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fse_set_steps": (ctypes.c_int, [_VP, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -263,6 +265,12 @@ class Context:
         rc = load().fse_lyapunov(self.h, _dp(Z), float(omega1), int(N_Ly), int(h), _dp(out))
         self._check(rc, (FSE_ENOCONV,))
         return out
+
+    def set_steps(self, n_steps):
+        self._check(load().fse_set_steps(self.h, int(n_steps)))
+
+    def profile(self, enable=True):
+        self._check(load().fse_profile(self.h, int(enable)))
 
     def timings(self):
         out = np.zeros(5)
