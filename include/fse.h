@@ -125,8 +125,11 @@ int fse_residual_jacobian(fse_ctx* ctx, const double* Z0, double omega1, double*
                           int want_jacobian, int* traj_status, int* newton_iters);
 
 /* Same on device memory: Z0_dev / R_dev are device pointers (2 n U~ doubles)
- * and the call is asynchronous on `stream` (a cudaStream_t; NULL = the
- * context stream).  The status of the run is read with fse_status(). */
+ * and the call is asynchronous with respect to the host.  `stream` (a
+ * cudaStream_t, NULL = the legacy default stream) is ordered before the
+ * evaluation and waits for its end; the work itself runs on the context's
+ * two streams (state path and sensitivities overlap).  The status of the run
+ * is read with fse_status(). */
 int fse_residual_jacobian_dev(fse_ctx* ctx, const double* Z0_dev, double omega1, double* R_dev,
                               int want_jacobian, void* stream);
 
@@ -182,8 +185,108 @@ int fse_profile(fse_ctx* ctx, int enable);
  * [1] the per-step state Newton + K_eff assembly + banded Cholesky,
  * [2] the sensitivity right-hand side, [3] the forward and [4] the backward
  * banded substitutions of the sensitivities (the latter includes the
- * Newmark update of the tangents).  Waits for the last evaluation. */
+ * Newmark update of the tangents), and [5] the mean number of in-loop
+ * refactorisations of the per-step Newton per trajectory-step.  Filled by
+ * fse_status() / the blocking entry points. */
 int fse_timings(fse_ctx* ctx, double* ms, int cap);
+
+/* ------------------------------------------------------------------------
+ * Learned continuation predictor (not in the paper).  A 3-layer MLP
+ * n_in -> n_hidden -> n_hidden -> n_out with the exact GELU
+ * gelu(z) = z (1 + erf(z / sqrt 2)) / 2 between layers maps normalised point
+ * parameters (w_1, w_2, F_1) to the coefficients of the torus in a POD basis of
+ * converged solutions.  Kernels keep weights, inputs and activations in BF16,
+ * accumulate in FP32 and keep FP32 master weights for Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  Loss: 1/(2B) sum (y - t)^2.
+ * Flat parameter order W1, b1, W2, b2, W3, b3 (W row-major, out x in).
+ * All data pointers are host float arrays, row-major (sample-major).
+ * ------------------------------------------------------------------------ */
+typedef struct fse_mlp fse_mlp;
+
+/* Create a network with zero parameters (set them with fse_mlp_set_params),
+ * batches up to max_batch samples; device < 0 uses the current device. */
+int fse_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, int device, fse_mlp** out);
+
+/* Free the network and its device memory; NULL is ignored. */
+void fse_mlp_destroy(fse_mlp* mlp);
+
+/* Number of parameters of the flat vector. */
+int fse_mlp_nparams(const fse_mlp* mlp);
+
+/* Number of outputs n_out. */
+int fse_mlp_nouts(const fse_mlp* mlp);
+
+/* Text of the last error of the network. */
+const char* fse_mlp_last_error(const fse_mlp* mlp);
+
+/* Set the FP32 master parameters (resets the Adam state). */
+int fse_mlp_set_params(fse_mlp* mlp, const float* flat);
+
+/* Copy the FP32 master parameters out. */
+int fse_mlp_get_params(fse_mlp* mlp, float* flat);
+
+/* Y (B x n_out) = network(X (B x n_in)), 1 <= B <= max_batch. */
+int fse_mlp_forward(fse_mlp* mlp, const float* X, int B, float* Y);
+
+/* Loss and gradient (flat, nullable) of the batch against the targets T. */
+int fse_mlp_grad(fse_mlp* mlp, const float* X, const float* T, int B, float* loss, float* grad);
+
+/* `steps` Adam steps of full-batch training with learning rate lr; loss (nullable)
+ * receives the loss after the last step. */
+int fse_mlp_train(fse_mlp* mlp, const float* X, const float* T, int B, int steps, float lr, float* loss);
+
+/* POD basis of m snapshots (rows of `snaps`, m x nu doubles): mean (nu), the r
+ * leading orthonormal modes (r x nu) of the mean-centred snapshots (method of
+ * snapshots: Jacobi eigen-decomposition of the m x m Gram matrix on the GPU)
+ * and their singular values (nullable).  r <= m <= 1024. */
+int fse_pod_build(const double* snaps, int nu, int m, int r, double* mean, double* basis, double* sing);
+
+/* ------------------------------------------------------------------------
+ * One-parameter continuation in w_1 (App. C, natural parameter with the
+ * frequency ratios fixed, Eq. Cont2).  Point j is predicted, then corrected by
+ * Newton on Eq. (16) at fixed w_1 until ||R||_2 <= rel_tol ||Z(0)||_2.
+ * Predictors: the secant through the last two accepted points, or the network
+ * (after `warmup` points): Z = mean + sum_k c_k mode_k with c from the MLP fed
+ * (w_1, w_2, F_1) normalised to [-1, 1] over [omega_lo, omega_hi]; the POD is
+ * rebuilt every pod_every points from all accepted points and the network is
+ * trained on their coefficients (each mode divided by its RMS over the
+ * accepted points, the scale the prediction multiplies back) for train_steps
+ * Adam steps after every point.  The outer linear solve is the dense LU of
+ * fse_newton_step (problems up to 16384 unknowns).
+ * ------------------------------------------------------------------------ */
+#define FSE_PRED_SECANT 0
+#define FSE_PRED_MLP 1
+
+typedef struct {
+    int n_points;              /* number of w_1 values                          */
+    const double* omega1;      /* host, n_points values in sweep order          */
+    int predictor;             /* FSE_PRED_SECANT or FSE_PRED_MLP               */
+    double rel_tol;            /* acceptance ||R|| <= rel_tol ||Z|| (1e-10)     */
+    int max_newton;            /* corrector iterations per point                */
+    int warmup;                /* points predicted by the secant before the MLP */
+    int pod_modes;             /* POD rank r = network outputs                  */
+    int pod_every;             /* POD rebuild period (points)                   */
+    int train_steps;           /* Adam steps after each accepted point          */
+    float lr;                  /* Adam learning rate                            */
+    double omega_lo, omega_hi; /* normalisation range of w_1                    */
+} fse_cont_opts;
+
+typedef struct {
+    int newton_iters;          /* corrector updates                             */
+    int evals;                 /* shooting evaluations (residual or Jacobian)   */
+    double res;                /* final ||R||_2                                 */
+    double znorm;              /* ||Z(0)||_2                                    */
+    double pred_err;           /* ||Z_pred - Z|| / ||Z|| of the predictor       */
+    double ms;                 /* device time of the point                      */
+    int status;                /* FSE_OK when accepted                          */
+    int predictor;             /* predictor actually used                       */
+} fse_cont_point;
+
+/* Run the sweep.  Z_start: host, 2 n U~ doubles (initial guess of point 0);
+ * Z_out: host, n_points x 2 n U~ (nullable); info: n_points records (nullable).
+ * mlp may be NULL for the secant predictor.  Returns the worst point status. */
+int fse_continue(fse_ctx* ctx, fse_mlp* mlp, const fse_cont_opts* opts, const double* Z_start,
+                 double* Z_out, fse_cont_point* info);
 
 #ifdef __cplusplus
 }

@@ -419,3 +419,86 @@ int lyapunov_run(fse_ctx* c, double w, int N_Ly, int h, double* sigma) {
 }
 
 }  // namespace fse
+
+// ----------------------------------------------------------------------------
+// small vector helpers of the outer solve and the continuation driver
+// ----------------------------------------------------------------------------
+
+namespace fse {
+
+// y = a x + b y
+__global__ void k_axpby(size_t n, double a, const double* x, double b, double* y) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = a * x[k] + b * y[k];
+}
+
+// out[0] = sum x^2, out[1] = sum y^2 (y may be null); one block
+__global__ void k_norms2(size_t n, const double* x, const double* y, double* out) {
+    __shared__ double ra[1024], rb[1024];
+    double a = 0.0, b = 0.0;
+    for (size_t k = threadIdx.x; k < n; k += blockDim.x) {
+        a += x[k] * x[k];
+        if (y) b += y[k] * y[k];
+    }
+    ra[threadIdx.x] = a;
+    rb[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ra[threadIdx.x] += ra[threadIdx.x + o];
+            rb[threadIdx.x] += rb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = ra[0];
+        out[1] = rb[0];
+    }
+}
+
+// z = mean + sum_k c_k basis[k]  (basis r x nu)
+__global__ void k_pod_expand(size_t nu, int r, const double* mean, const double* basis, const double* coef,
+                             double* z) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nu; x += (size_t)gridDim.x * blockDim.x) {
+        double acc = mean[x];
+        for (int k = 0; k < r; ++k) acc += coef[k] * basis[(size_t)k * nu + x];
+        z[x] = acc;
+    }
+}
+
+// coef[j][k] = basis[k] . (Z[j] - mean), one block per (j, k)
+__global__ void k_pod_project(size_t nu, int r, const double* mean, const double* basis, const double* Z,
+                              double* coef) {
+    const int j = blockIdx.x, k = blockIdx.y;
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (size_t x = threadIdx.x; x < nu; x += blockDim.x)
+        acc += basis[(size_t)k * nu + x] * (Z[(size_t)j * nu + x] - mean[x]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) coef[(size_t)j * r + k] = red[0];
+}
+
+void vec_axpby(fse_ctx* c, size_t n, double a, const double* x, double b, double* y) {
+    k_axpby<<<nblocks(n, 256), 256, 0, c->stream>>>(n, a, x, b, y);
+}
+
+void vec_norms2(fse_ctx* c, size_t n, const double* x, const double* y, double* out_dev) {
+    k_norms2<<<1, 1024, 0, c->stream>>>(n, x, y, out_dev);
+}
+
+void pod_expand(fse_ctx* c, size_t nu, int r, const double* mean, const double* basis, const double* coef,
+                double* z) {
+    k_pod_expand<<<nblocks(nu, 256), 256, 0, c->stream>>>(nu, r, mean, basis, coef, z);
+}
+
+void pod_project(fse_ctx* c, size_t nu, int r, int m, const double* mean, const double* basis, const double* Z,
+                 double* coef) {
+    k_pod_project<<<dim3(m, r), 256, 0, c->stream>>>(nu, r, mean, basis, Z, coef);
+}
+
+}  // namespace fse

@@ -72,7 +72,7 @@ static void free_ctx(fse_ctx* c) {
                     c->d.kt_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
                     c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
                     c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
-                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->Jd, c->piv};
+                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->Jd, c->piv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -166,6 +166,13 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         return rc;
     }
     for (auto& e : c->ev) cudaEventCreateWithFlags(&e, cudaEventDefault);
+    // ordering events of the two-stream step loop (one pair per Newmark step)
+    c->ev_state.assign(p.S1, nullptr);
+    c->ev_sens.assign(p.S1, nullptr);
+    for (int k = 0; k < p.S1; ++k) {
+        cudaEventCreateWithFlags(&c->ev_state[k], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_sens[k], cudaEventDisableTiming);
+    }
     // harmonic table
     auto rows = harmonic_rows(H);
     const int dm1 = p.d - 1;
@@ -277,7 +284,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.nnz_kt = (int)kcol.size();
     p.nblk = (n + FSE_BLK - 1) / FSE_BLK;
     p.ld = (p.P + 3) & ~3;
-    p.RW = 2 * b + 8;
+    p.RW = 2 * b + 2 * FSE_RHS_G;
     p.RWT = 1;
     while (p.RWT < b + FSE_BLK) p.RWT <<= 1;
     std::vector<int> cslot(ccol.size()), kslot(kcol.size());
@@ -287,7 +294,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.smem_rhs = fse::rhs_smem(p);
     p.smem_trsm = fse::trsm_smem(p);
     const size_t lim = 220 * 1024;
-    if (p.smem_state > lim || p.smem_rhs > lim || p.smem_trsm > lim ||
+    if (b > FSE_MAX_BAND || p.smem_state > lim || p.smem_rhs > lim || p.smem_trsm > lim ||
         (size_t)nb * nb * sizeof(double) + (size_t)(b * nb / 2 + 2) * 4 > lim) {
         free_ctx(c);
         return set_err(nullptr, FSE_EINVAL, "n or half-bandwidth too large for the on-chip working set");
@@ -353,6 +360,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     A(&c->d.vec2, nu * 8);
     A(&c->d.status, (size_t)N * 4);
     A(&c->d.iters, (size_t)N * 4);
+    A(&c->d.nref, (size_t)N * 4);
     if (e != cudaSuccess) {
         rc = cuda_check(c, e, "device allocation");
         g_setup_err = c->err;
@@ -387,6 +395,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     cudaMemcpyAsync(c->d.ktab, c->ktab_host.data(), c->ktab_host.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(c->d.status, 0, (size_t)N * 4, st);
     cudaMemsetAsync(c->d.iters, 0, (size_t)N * 4, st);
+    cudaMemsetAsync(c->d.nref, 0, (size_t)N * 4, st);
     fse::launch_fill_tables(c);
     const int bad = fse::launch_factor_M(c);
     rc = cuda_check(c, cudaStreamSynchronize(st), "setup");
@@ -514,6 +523,11 @@ static int collect_status(fse_ctx* c, int* ts, int* it) {
             c->timing[1 + ph] = tot;
         }
         c->prof_pending = false;
+        std::vector<int> nr(N);
+        cudaMemcpy(nr.data(), c->d.nref, N * 4, cudaMemcpyDeviceToHost);
+        double tot = 0.0;
+        for (int x : nr) tot += x;
+        c->timing[5] = steps > 0 ? tot / ((double)N * steps) : 0.0;
     }
     if (ts) std::memcpy(ts, st.data(), N * 4);
     if (it) std::memcpy(it, its.data(), N * 4);
@@ -529,17 +543,15 @@ static int collect_status(fse_ctx* c, int* ts, int* it) {
 extern "C" int fse_residual_jacobian_dev(fse_ctx* c, const double* Z0_dev, double w, double* R_dev,
                                          int sens, void* stream) {
     if (!c || !Z0_dev || !R_dev) return FSE_EINVAL;
+    // the caller's stream (NULL = the legacy default stream) is ordered before the evaluation
+    // and waits for its end; the evaluation itself runs on the context's own streams
     cudaStream_t user = (cudaStream_t)stream;
-    if (user && user != c->stream) {
-        // order the context stream after the caller's stream, and the caller's after the result
-        cudaEventRecord(c->ev[6], user);
-        cudaStreamWaitEvent(c->stream, c->ev[6], 0);
-    }
+    cudaSetDevice(c->device);
+    cudaEventRecord(c->ev[6], user);
+    cudaStreamWaitEvent(c->stream, c->ev[6], 0);
     int rc = run_eval(c, Z0_dev, w, R_dev, sens);
-    if (user && user != c->stream) {
-        cudaEventRecord(c->ev[7], c->stream);
-        cudaStreamWaitEvent(user, c->ev[7], 0);
-    }
+    cudaEventRecord(c->ev[7], c->stream);
+    cudaStreamWaitEvent(user, c->ev[7], 0);
     return rc;
 }
 
@@ -634,35 +646,55 @@ extern "C" int fse_monodromy(fse_ctx* c, double* Phi, double* dzdw) {
     return rc;
 }
 
+// ||R||_2 and ||Z(0)||_2 of the last evaluation (device reduction, two scalars back)
+static int norms_RZ(fse_ctx* c, double* rn, double* zn) {
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    fse::vec_norms2(c, m, c->d.R, c->d.Z0, c->d.vec2);
+    double h[2];
+    cudaMemcpyAsync(h, c->d.vec2, 16, cudaMemcpyDeviceToHost, c->stream);
+    const int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "norms");
+    if (rn) *rn = std::sqrt(h[0]);
+    if (zn) *zn = std::sqrt(h[1]);
+    return rc;
+}
+
+// Residual (sens = 0) or residual + Jacobian (sens = 1) at the device iterate d.Z0
+static int eval_at_iterate(fse_ctx* c, double w, int sens, double* rn, double* zn) {
+    int rc = run_eval(c, c->d.Z0, w, c->d.R, sens);
+    if (rc) return rc;
+    const int st = collect_status(c, nullptr, nullptr);
+    if (st < 0 && st != FSE_ENOCONV) return st;
+    rc = norms_RZ(c, rn, zn);
+    return rc ? rc : st;
+}
+
+// Solve J dZ = -R (Jacobian and R of the last evaluation) and update d.Z0 += dZ, on the device.
+static int newton_solve_update(fse_ctx* c) {
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    if (m > 16384) return set_err(c, FSE_EINVAL, "outer solve: dense LU limited to 16384 unknowns");
+    int rc = ensure_dense(c, m);
+    if (rc) return rc;
+    fse::launch_dense_jac(c, c->Jd);
+    fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, c->d.vec);       // rhs = -R
+    rc = fse::dense_lu_solve(c, c->Jd, c->d.vec, (int)m);
+    if (rc) return set_err(c, rc, "singular shooting Jacobian");
+    fse::vec_axpby(c, m, 1.0, c->d.vec, 1.0, c->d.Z0);       // Z0 += dZ
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "newton update");
+}
+
 extern "C" int fse_newton_step(fse_ctx* c, double* Z0, double w, double* res_norm) {
     if (!c || !Z0) return FSE_EINVAL;
     const size_t m = (size_t)2 * c->p.n * c->p.U;
     if (m > 16384) return set_err(c, FSE_EINVAL, "fse_newton_step: dense solve limited to 16384 unknowns");
     cudaSetDevice(c->device);
-    int rc = ensure_dense(c, m);
-    if (rc) return rc;
     cudaMemcpyAsync(c->d.Z0, Z0, m * 8, cudaMemcpyHostToDevice, c->stream);
-    rc = run_eval(c, c->d.Z0, w, c->d.R, 1);
-    if (rc) return rc;
-    std::vector<double> R(m);
-    cudaMemcpyAsync(R.data(), c->d.R, m * 8, cudaMemcpyDeviceToHost, c->stream);
-    const int st = collect_status(c, nullptr, nullptr);
+    const int st = eval_at_iterate(c, w, 1, res_norm, nullptr);
     if (st < 0 && st != FSE_ENOCONV) return st;
-    double nr = 0.0;
-    for (double x : R) nr += x * x;
-    if (res_norm) *res_norm = std::sqrt(nr);
-    fse::launch_dense_jac(c, c->Jd);
-    // rhs = -R
-    for (double& x : R) x = -x;
-    cudaMemcpyAsync(c->d.vec, R.data(), m * 8, cudaMemcpyHostToDevice, c->stream);
-    rc = fse::dense_lu_solve(c, c->Jd, c->d.vec, (int)m);
-    if (rc) return set_err(c, rc, "singular shooting Jacobian");
-    std::vector<double> dZ(m);
-    cudaMemcpyAsync(dZ.data(), c->d.vec, m * 8, cudaMemcpyDeviceToHost, c->stream);
-    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step");
+    int rc = newton_solve_update(c);
     if (rc) return rc;
-    for (size_t k = 0; k < m; ++k) Z0[k] += dZ[k];
-    return st;
+    cudaMemcpyAsync(Z0, c->d.Z0, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step");
+    return rc ? rc : st;
 }
 
 extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, int h, double* sigma) {
@@ -701,6 +733,194 @@ extern "C" int fse_profile(fse_ctx* c, int enable) {
 
 extern "C" int fse_timings(fse_ctx* c, double* ms, int cap) {
     if (!c || !ms) return FSE_EINVAL;
-    for (int k = 0; k < cap && k < 5; ++k) ms[k] = c->timing[k];
+    for (int k = 0; k < cap && k < 6; ++k) ms[k] = c->timing[k];
     return FSE_OK;
+}
+
+// ----------------------------------------------------------------------------
+// one-parameter continuation in w_1 with the secant or the learned predictor
+// ----------------------------------------------------------------------------
+
+extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, const double* Z_start,
+                            double* Z_out, fse_cont_point* info) {
+    if (!c || !o || !Z_start || !o->omega1 || o->n_points < 1) return FSE_EINVAL;
+    if (o->predictor == FSE_PRED_MLP && !mlp) return set_err(c, FSE_EINVAL, "learned predictor needs a network");
+    if (!(o->rel_tol > 0.0) || o->max_newton < 0) return set_err(c, FSE_EINVAL, "bad tolerance or iteration limit");
+    cudaSetDevice(c->device);
+    const size_t nu = (size_t)2 * c->p.n * c->p.U;
+    const int P = o->n_points;
+    if (o->predictor == FSE_PRED_MLP && (o->pod_modes < 1 || fse_mlp_nouts(mlp) != o->pod_modes))
+        return set_err(c, FSE_EINVAL, "network outputs must equal pod_modes");
+    double *Zs = nullptr, *Zp = nullptr, *Sscr = nullptr, *pmean = nullptr, *pbasis = nullptr, *coef = nullptr,
+           *cdev = nullptr;
+    cudaError_t e = cudaMalloc(&Zs, (size_t)P * nu * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&Zp, nu * 8);
+    const bool learn = o->predictor == FSE_PRED_MLP;
+    const int rmax = std::max(1, o->pod_modes);
+    if (learn) {
+        if (e == cudaSuccess) e = cudaMalloc(&Sscr, (size_t)P * nu * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&pmean, nu * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&pbasis, (size_t)rmax * nu * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&coef, (size_t)P * rmax * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&cdev, (size_t)rmax * 8);
+    }
+    auto cleanup = [&]() {
+        for (void* q : {(void*)Zs, (void*)Zp, (void*)Sscr, (void*)pmean, (void*)pbasis, (void*)coef, (void*)cdev})
+            if (q) cudaFree(q);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_check(c, e, "continuation buffers");
+    }
+    int r = 0;                                 // current POD rank (0 = no basis yet)
+    int reff = 0;                              // modes above the relative threshold 1e-10
+    double tmax = 0.0;                         // clamp of the scaled network outputs
+    std::vector<double> sing(rmax, 0.0);
+    std::vector<double> tsc(rmax, 1.0);        // per-mode scale: RMS of the training coefficients
+    const double lo = o->omega_lo, hi = o->omega_hi > o->omega_lo ? o->omega_hi : o->omega_lo + 1.0;
+    auto feats = [&](double w, float* x) {
+        const double t = 2.0 * (w - lo) / (hi - lo) - 1.0;
+        x[0] = (float)t;
+        x[1] = (float)t;                        // w_2 = rho w_1: same normalised value
+        x[2] = 0.0f;                            // F_1 fixed over the sweep
+    };
+    int worst = FSE_OK;
+    for (int j = 0; j < P; ++j) {
+        const double w = o->omega1[j];
+        cudaEventRecord(c->ev[4], c->stream);
+        // ---- predictor
+        bool used_mlp = false;
+        if (j == 0) {
+            cudaMemcpyAsync(c->d.Z0, Z_start, nu * 8, cudaMemcpyHostToDevice, c->stream);
+        } else if (learn && reff > 0 && j >= std::max(2, o->warmup)) {
+            float x[3];
+            feats(w, x);
+            std::vector<float> yy((size_t)rmax);
+            int rc = fse_mlp_forward(mlp, x, 1, yy.data());
+            if (rc) {
+                cleanup();
+                return set_err(c, rc, "network forward failed");
+            }
+            std::vector<double> cc(r, 0.0);
+            for (int k = 0; k < reff; ++k) {
+                const double t = std::max(-tmax, std::min(tmax, (double)yy[k]));
+                cc[k] = t * tsc[k];
+            }
+            cudaMemcpyAsync(cdev, cc.data(), r * 8, cudaMemcpyHostToDevice, c->stream);
+            fse::pod_expand(c, nu, r, pmean, pbasis, cdev, c->d.Z0);
+            used_mlp = true;
+        } else if (j == 1) {
+            cudaMemcpyAsync(c->d.Z0, Zs, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+        } else {
+            const double q = (w - o->omega1[j - 1]) / (o->omega1[j - 1] - o->omega1[j - 2]);
+            cudaMemcpyAsync(c->d.Z0, Zs + (size_t)(j - 1) * nu, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+            fse::vec_axpby(c, nu, -q, Zs + (size_t)(j - 2) * nu, 1.0 + q, c->d.Z0);   // (1+q) Z_{j-1} - q Z_{j-2}
+        }
+        cudaMemcpyAsync(Zp, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+        // ---- corrector: Newton on Eq. (16) at fixed w_1, accepted when ||R|| <= tol ||Z||
+        double rn = 0.0, zn = 0.0;
+        int it = 0, evals = 1;
+        int st = eval_at_iterate(c, w, 1, &rn, &zn);
+        if (used_mlp && (st < FSE_ENOCONV || !std::isfinite(rn))) {
+            // the network prediction left the basin: fall back to the secant prediction
+            const double q = (w - o->omega1[j - 1]) / (o->omega1[j - 1] - o->omega1[j - 2]);
+            cudaMemcpyAsync(c->d.Z0, Zs + (size_t)(j - 1) * nu, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+            fse::vec_axpby(c, nu, -q, Zs + (size_t)(j - 2) * nu, 1.0 + q, c->d.Z0);
+            cudaMemcpyAsync(Zp, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+            used_mlp = false;
+            st = eval_at_iterate(c, w, 1, &rn, &zn);
+            ++evals;
+        }
+        while (st >= FSE_ENOCONV && rn > o->rel_tol * zn && it < o->max_newton) {
+            int rc = newton_solve_update(c);
+            if (rc) {
+                st = rc;
+                break;
+            }
+            ++it;
+            st = eval_at_iterate(c, w, 0, &rn, &zn);
+            ++evals;
+            if (rn <= o->rel_tol * zn || st < FSE_ENOCONV) break;
+            st = eval_at_iterate(c, w, 1, &rn, &zn);
+            ++evals;
+        }
+        const int pst = (st < 0) ? st : (rn <= o->rel_tol * zn ? FSE_OK : FSE_ENOCONV);
+        if (pst != FSE_OK && (worst == FSE_OK || pst < worst)) worst = pst;
+        cudaMemcpyAsync(Zs + (size_t)j * nu, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+        if (Z_out) cudaMemcpyAsync(Z_out + (size_t)j * nu, c->d.Z0, nu * 8, cudaMemcpyDeviceToHost, c->stream);
+        // prediction error ||Z_pred - Z*|| / ||Z*||
+        fse::vec_axpby(c, nu, 1.0, c->d.Z0, -1.0, Zp);
+        fse::vec_norms2(c, nu, Zp, c->d.Z0, c->d.vec2);
+        double h2[2];
+        cudaMemcpyAsync(h2, c->d.vec2, 16, cudaMemcpyDeviceToHost, c->stream);
+        cudaEventRecord(c->ev[5], c->stream);
+        int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "continuation point");
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+        if (info) {
+            info[j].newton_iters = it;
+            info[j].evals = evals;
+            info[j].res = rn;
+            info[j].znorm = zn;
+            info[j].pred_err = std::sqrt(h2[0]) / std::max(std::sqrt(h2[1]), 1e-300);
+            info[j].ms = ms;
+            info[j].status = pst;
+            info[j].predictor = used_mlp ? FSE_PRED_MLP : FSE_PRED_SECANT;
+        }
+        // ---- learning: POD of the accepted tori, network trained on their coefficients
+        if (learn && j >= 1) {
+            const int m = j + 1;
+            const bool rebuild = (m % std::max(1, o->pod_every) == 0) || r == 0;
+            if (rebuild) {
+                const int rr = std::min(rmax, m - 1);
+                cudaMemcpyAsync(Sscr, Zs, (size_t)m * nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+                rc = fse::pod_build_dev(Sscr, (int)nu, m, rr, pmean, pbasis, sing.data(), c->stream);
+                if (rc) {
+                    cleanup();
+                    return set_err(c, rc, "POD build failed");
+                }
+                r = rr;
+                reff = 0;
+                while (reff < r && sing[reff] > 1e-10 * sing[0]) ++reff;
+            }
+            fse::pod_project(c, nu, r, m, pmean, pbasis, Zs, coef);
+            std::vector<double> ch((size_t)m * r);
+            cudaMemcpyAsync(ch.data(), coef, ch.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+            rc = cuda_check(c, cudaStreamSynchronize(c->stream), "POD projection");
+            if (rc) {
+                cleanup();
+                return rc;
+            }
+            const int no = o->pod_modes;
+            std::vector<float> X((size_t)m * 3), T((size_t)m * no, 0.0f);
+            // targets: coefficients divided by their RMS over the training set, mode by mode
+            // (modes below the rank threshold are not learned)
+            tmax = 0.0;
+            for (int k = 0; k < reff; ++k) {
+                double s2 = 0.0;
+                for (int a = 0; a < m; ++a) s2 += ch[(size_t)a * r + k] * ch[(size_t)a * r + k];
+                tsc[k] = std::max(std::sqrt(s2 / m), 1e-300);
+            }
+            for (int a = 0; a < m; ++a) {
+                feats(o->omega1[a], &X[(size_t)a * 3]);
+                for (int k = 0; k < reff; ++k) {
+                    const double t = ch[(size_t)a * r + k] / tsc[k];
+                    T[(size_t)a * no + k] = (float)t;
+                    tmax = std::max(tmax, 2.0 * std::fabs(t));
+                }
+            }
+            float loss = 0.f;
+            rc = fse_mlp_train(mlp, X.data(), T.data(), m, o->train_steps, o->lr, &loss);
+            if (rc) {
+                cleanup();
+                return set_err(c, rc, "network training failed");
+            }
+        }
+    }
+    cleanup();
+    return worst;
 }

@@ -12,6 +12,8 @@
 #define FSE_BLK 32        // row block of the blocked triangular solves
 #define FSE_NBUF_F 2      // factor buffers (step parity)
 #define FSE_NBUF_KT 3     // tangent-value buffers (step index mod 3)
+#define FSE_RHS_G 16      // rows per step of the right-hand-side kernel (2 per warp)
+#define FSE_MAX_BAND 224  // half-bandwidth limit of the blocked solves
 
 namespace fse {
 
@@ -89,13 +91,14 @@ struct Dev {
     double* yb = nullptr;    // N x 2n scratch
     int* status = nullptr;   // N
     int* iters = nullptr;    // N
+    int* nref = nullptr;     // N  in-loop refactorisations of the per-step Newton
 };
 
 struct Params {
     int n = 0, b = 0, d = 0, e = 0, N = 0, U = 0, L = 0, S1 = 0, P = 0;
     int maxit = 0, prec = 0, ncolors = 0, n_el = 0, nnz = 0, nnz_kt = 0, nblk = 0;
     int ld = 0;              // row stride of the tangent arrays: P rounded up to a multiple of 4
-    int RW = 0;              // ring rows of the right-hand-side kernel (2b + 8)
+    int RW = 0;              // ring rows of the right-hand-side kernel (2b + 2 FSE_RHS_G)
     int RWT = 0;             // ring rows of the blocked solves (power of two >= b + 32)
     double tol = 0;
     size_t smem_state = 0, smem_rhs = 0, smem_trsm = 0;
@@ -117,7 +120,7 @@ struct fse_ctx {
     double omega_jac = 0.0;
     cudaEvent_t ev[8] = {};
     std::vector<cudaEvent_t> ev_state, ev_sens;   // per-step ordering events
-    double timing[5] = {0, 0, 0, 0, 0};
+    double timing[6] = {0, 0, 0, 0, 0, 0};
     // optional per-kernel timing: events around every launch of the step loop
     bool prof = false;
     int n_steps = 0;                // 0 = the whole period
@@ -156,5 +159,18 @@ void launch_phi_copy(fse_ctx* c, double* Phi_dev, double* dzdw_dev);
 void launch_dense_jac(fse_ctx* c, double* J);
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
+
+// vector helpers on the context stream (fse_aft.cu)
+void vec_axpby(fse_ctx* c, size_t n, double a, const double* x, double b, double* y);
+void vec_norms2(fse_ctx* c, size_t n, const double* x, const double* y, double* out_dev);
+void pod_expand(fse_ctx* c, size_t nu, int r, const double* mean, const double* basis, const double* coef,
+                double* z);
+void pod_project(fse_ctx* c, size_t nu, int r, int m, const double* mean, const double* basis, const double* Z,
+                 double* coef);
+
+// POD of m device snapshots (rows of S, m x nu; S is centred in place) on `st`:
+// mean (nu), r modes (r x nu) on the device, singular values on the host (fse_mlp.cu)
+int pod_build_dev(double* S, int nu, int m, int r, double* mean, double* basis, double* sing_host,
+                  cudaStream_t st);
 
 }  // namespace fse

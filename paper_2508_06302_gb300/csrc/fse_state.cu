@@ -97,6 +97,8 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
         const int c = idx / nb;
         wnd[idx] = (c < n) ? Ac[(size_t)c * nb + (idx - c * nb)] : T(0);
     }
+    // the column entering the window at step j (column j + nb) is fetched one step ahead
+    T pref = (tid < nb && nb < n) ? Ac[(size_t)nb * nb + tid] : T(0);
     __syncthreads();
     int slot = 0;   // window slot of column j (= j mod nb)
     for (int j = 0; j < n; ++j, slot = (slot + 1 == nb) ? 0 : slot + 1) {
@@ -125,7 +127,8 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
         // write column j of L out and load column j + nb into its slot (each thread owns
         // the same entries r in both parts, so no barrier is needed between them)
         const int jn = j + nb;
-        for (int r = tid; r < nb; r += nt) {
+        if (tid < nb) {   // nb <= blockDim.x: one entry per thread
+            const int r = tid;
             const T v = (j + r < n) ? (r == 0 ? ljj : colj[r] * inv) : T(0);
             Ac[(size_t)j * nb + r] = v;
             if (j + r < n) Lr[(size_t)(j + r) * nb + (b - r)] = v;
@@ -133,7 +136,8 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
                 Linv[j] = inv;
                 for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
             }
-            colj[r] = (jn < n) ? Ac[(size_t)jn * nb + r] : T(0);
+            colj[r] = (jn < n) ? pref : T(0);
+            pref = (jn + 1 < n) ? Ac[(size_t)(jn + 1) * nb + r] : T(0);
         }
         __syncthreads();
     }
@@ -190,7 +194,7 @@ struct StateArgs {
     double *q, *u, *a;
     const void *cLc, *cLr, *cLinv, *cDinv;   // chord factor (regular steps)
     void *oLc, *oLr, *oLinv, *oDinv;         // factor of K_eff at the new state
-    int *status, *iters;
+    int *status, *iters, *nref;
 };
 
 __device__ __forceinline__ double forcing_i(const StateArgs& A, int s, int i, double phi) {
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         if (!A.init) sa[i] = A.a[off + i];
     }
     __syncthreads();
-    int it = 0;
+    int it = 0, nref = 0;
     if (A.init) {
         // consistent start: w^2 M a0 = e(0) - w D u0 - K q0 - f_nl(q0)  (Eq. E2 at phi_1 = 0)
         for (int i = tid; i < n; i += nt) sr[i] = 0.0;
@@ -436,7 +440,11 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
                 ++it;
                 break;
             }
-            if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit) {
+            // an FP32 factor limits the chord contraction by itself: one refactorisation per
+            // step is enough to tell nonlinearity from rounding, more would only repeat it
+            const bool allow = sizeof(T) == 8 || nref == 0;
+            if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
+                ++nref;
                 assemble_keff<T>(A, s, sqn, oLc, kt_out);
                 if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
@@ -483,6 +491,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
         A.status[s] = s_stat;
         A.iters[s] = (A.init ? 0 : A.iters[s]) + it;
+        A.nref[s] = (A.init ? 0 : A.nref[s]) + nref;
     }
 }
 
@@ -617,6 +626,7 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.oDinv = (char*)c->d.Dinv + fo * dsz;
     A.status = c->d.status;
     A.iters = c->d.iters;
+    A.nref = c->d.nref;
     return A;
 }
 

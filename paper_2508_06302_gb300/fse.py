@@ -50,6 +50,7 @@ class fse_opts(ctypes.Structure):
 
 _lib = None
 _DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.POINTER(ctypes.c_float)
 _IP = ctypes.POINTER(ctypes.c_int)
 _VP = ctypes.c_void_p
 
@@ -90,6 +91,17 @@ def load(path: Optional[str] = None):
         "fse_timings": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
         "fse_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
         "fse_set_steps": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fse_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_VP)]),
+        "fse_mlp_destroy": (None, [_VP]),
+        "fse_mlp_nparams": (ctypes.c_int, [_VP]),
+        "fse_mlp_last_error": (ctypes.c_char_p, [_VP]),
+        "fse_mlp_set_params": (ctypes.c_int, [_VP, _FP]),
+        "fse_mlp_get_params": (ctypes.c_int, [_VP, _FP]),
+        "fse_mlp_forward": (ctypes.c_int, [_VP, _FP, ctypes.c_int, _FP]),
+        "fse_mlp_grad": (ctypes.c_int, [_VP, _FP, _FP, ctypes.c_int, _FP, _FP]),
+        "fse_mlp_train": (ctypes.c_int, [_VP, _FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_float, _FP]),
+        "fse_pod_build": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +285,129 @@ class Context:
         self._check(load().fse_profile(self.h, int(enable)))
 
     def timings(self):
-        out = np.zeros(5)
-        load().fse_timings(self.h, _dp(out), 5)
+        out = np.zeros(6)
+        load().fse_timings(self.h, _dp(out), 6)
         return out
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(_FP)
+
+
+class Mlp:
+    """The BF16 predictor network (fse_mlp_*)."""
+
+    ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+    def __init__(self, n_in=3, n_hidden=256, n_out=64, max_batch=512, device=-1):
+        lib = load()
+        h = _VP()
+        rc = lib.fse_mlp_create(n_in, n_hidden, n_out, max_batch, device, ctypes.byref(h))
+        if rc:
+            raise FSEError(rc, "fse_mlp_create")
+        self.h = h.value
+        self.dims = (n_in, n_hidden, n_out)
+        self.np = lib.fse_mlp_nparams(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fse_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise FSEError(rc, load().fse_mlp_last_error(self.h).decode())
+
+    def set_params(self, params):
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
+                                                    for k in self.ORDER]), dtype=np.float32)
+        assert flat.size == self.np
+        self._check(load().fse_mlp_set_params(self.h, _fp(flat)))
+
+    def get_params(self):
+        flat = np.zeros(self.np, np.float32)
+        self._check(load().fse_mlp_get_params(self.h, _fp(flat)))
+        return flat
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], self.dims[2]), np.float32)
+        self._check(load().fse_mlp_forward(self.h, _fp(X), X.shape[0], _fp(Y)))
+        return Y
+
+    def grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = np.zeros(1, np.float32)
+        g = np.zeros(self.np, np.float32)
+        self._check(load().fse_mlp_grad(self.h, _fp(X), _fp(T), X.shape[0], _fp(loss), _fp(g)))
+        return float(loss[0]), g
+
+    def train(self, X, T, steps, lr):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(load().fse_mlp_train(self.h, _fp(X), _fp(T), X.shape[0], int(steps), float(lr), _fp(loss)))
+        return float(loss[0])
+
+
+def fse_pod_build(snaps, r):
+    """POD of the rows of snaps (m x nu): mean, r modes (r x nu), singular values."""
+    S = np.ascontiguousarray(snaps, dtype=np.float64)
+    m, nu = S.shape
+    mean = np.zeros(nu)
+    basis = np.zeros((r, nu))
+    sing = np.zeros(r)
+    rc = load().fse_pod_build(_dp(S), nu, m, r, _dp(mean), _dp(basis), _dp(sing))
+    if rc:
+        raise FSEError(rc, "fse_pod_build")
+    return mean, basis, sing
+
+
+FSE_PRED_SECANT = 0
+FSE_PRED_MLP = 1
+
+
+class fse_cont_opts(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int), ("omega1", _DP), ("predictor", ctypes.c_int),
+                ("rel_tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("warmup", ctypes.c_int),
+                ("pod_modes", ctypes.c_int), ("pod_every", ctypes.c_int), ("train_steps", ctypes.c_int),
+                ("lr", ctypes.c_float), ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double)]
+
+
+class fse_cont_point(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("evals", ctypes.c_int), ("res", ctypes.c_double),
+                ("znorm", ctypes.c_double), ("pred_err", ctypes.c_double), ("ms", ctypes.c_double),
+                ("status", ctypes.c_int), ("predictor", ctypes.c_int)]
+
+
+def fse_continue(ctx, omegas, Z_start, predictor="secant", mlp=None, rel_tol=1e-10, max_newton=10,
+                 warmup=8, pod_modes=64, pod_every=8, train_steps=200, lr=1e-3, omega_range=None):
+    """fse_continue(): returns (Z (n_points x nu), list of per-point dicts, rc)."""
+    lib = load()
+    if not hasattr(lib, "_cont_sig"):
+        lib.fse_continue.restype = ctypes.c_int
+        lib.fse_continue.argtypes = [_VP, _VP, ctypes.POINTER(fse_cont_opts), _DP, _DP,
+                                     ctypes.POINTER(fse_cont_point)]
+        lib.fse_mlp_nouts.restype = ctypes.c_int
+        lib.fse_mlp_nouts.argtypes = [_VP]
+        lib._cont_sig = True
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    P = om.size
+    lo, hi = (float(om.min()), float(om.max())) if omega_range is None else omega_range
+    o = fse_cont_opts(P, _dp(om), FSE_PRED_MLP if predictor == "mlp" else FSE_PRED_SECANT, rel_tol, max_newton,
+                      warmup, pod_modes, pod_every, train_steps, lr, lo, hi)
+    Z0 = np.ascontiguousarray(Z_start, dtype=np.float64)
+    Zout = np.zeros((P, Z0.size))
+    info = (fse_cont_point * P)()
+    rc = lib.fse_continue(ctx.h, mlp.h if mlp is not None else None, ctypes.byref(o), _dp(Z0), _dp(Zout), info)
+    if rc not in (FSE_OK, FSE_ENOCONV):
+        raise FSEError(rc, fse_last_error(ctx.h))
+    pts = [{k: getattr(info[j], k) for k, _ in fse_cont_point._fields_} for j in range(P)]
+    return Zout, pts, rc

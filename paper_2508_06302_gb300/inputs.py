@@ -546,3 +546,21 @@ def random_coeffs(n: int, U_tilde: int, scale: float, seed: int) -> np.ndarray:
     """Seeded random Fourier coefficient vector Z(0) (state-major, 2n*U~)."""
     rng = np.random.default_rng(seed)
     return scale * rng.standard_normal(2 * n * U_tilde)
+
+
+def mlp_init(n_in: int = 3, n_hidden: int = 256, n_out: int = 64, seed: int = 0) -> dict:
+    """Seeded Glorot-uniform weights and zero biases of the 3-layer predictor MLP.
+
+    Draw order: W1, W2, W3 (each row-major, out x in).
+    """
+    rng = np.random.default_rng(seed)
+
+    def glorot(fo, fi):
+        lim = math.sqrt(6.0 / (fi + fo))
+        return rng.uniform(-lim, lim, (fo, fi))
+
+    W1 = glorot(n_hidden, n_in)
+    W2 = glorot(n_hidden, n_hidden)
+    W3 = glorot(n_out, n_hidden)
+    return {"W1": W1, "b1": np.zeros(n_hidden), "W2": W2, "b2": np.zeros(n_hidden),
+            "W3": W3, "b3": np.zeros(n_out)}
