@@ -169,6 +169,30 @@ int fse_newton_step(fse_ctx* ctx, double* Z0, double omega1, double* res_norm_ou
 int fse_lyapunov(fse_ctx* ctx, const double* Z0, double omega1, int N_Ly, int h,
                  double* sigma_out);
 
+/* Size limits of fse_lyapunov_noalloc: 2 n h doubles for each of its Q and A
+ * blocks, and N trajectories. */
+#define FSE_NOALLOC_MAX_QH 262144
+#define FSE_NOALLOC_MAX_N 65536
+
+/* fse_lyapunov without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc or cudaFree
+ * while they run -- a process that gives all device memory to its own pool at
+ * start-up and allows no other allocation, or a latency-bound loop that cannot
+ * take the device-wide synchronisation cudaFree implies.  Arguments, result and
+ * status are those of fse_lyapunov; the trajectory buffers are the context's
+ * (allocated once by fse_setup) and the propagation scratch is one static
+ * device array of 4.5 MiB that every GPU loading this library holds until the
+ * process exits.  Limits: h <= 64, 2 n h <= FSE_NOALLOC_MAX_QH,
+ * N <= FSE_NOALLOC_MAX_N; a larger size returns FSE_EINVAL (message in
+ * fse_last_error) before anything runs.  The first call on a device looks up
+ * the array's device address and caches it: make that first call before any
+ * stream capture on that device.  Every call in the process shares the array,
+ * which keeps the last call's contents (each call re-initialises what it
+ * needs); calls that overlap on the GPU -- from other contexts, streams or
+ * host threads -- race on it, so the caller must serialise them. */
+int fse_lyapunov_noalloc(fse_ctx* ctx, const double* Z0, double omega1, int N_Ly, int h,
+                         double* sigma_out);
+
 /* Integrate only the first n_steps (> 0) Newmark steps of the period in the
  * following evaluations; 0 restores the full period S1.  With n_steps < S1
  * the "residual" is the DFT of the truncated trajectories' end states minus

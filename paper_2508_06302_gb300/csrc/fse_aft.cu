@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "fse_common.cuh"
@@ -413,6 +414,112 @@ int lyapunov_run(fse_ctx* c, double w, int N_Ly, int h, double* sigma) {
     cudaFree(acc);
     cudaFree(wts);
     if (e != cudaSuccess) return FSE_ECUDA;
+    const double T1 = 2.0 * M_PI / w;
+    for (int j = 0; j < h; ++j) sigma[j] = hacc[j] / (N_Ly * T1);
+    return FSE_OK;
+}
+
+}  // namespace fse
+
+// ----------------------------------------------------------------------------
+// Lyapunov propagation with static device scratch (no allocation)
+// ----------------------------------------------------------------------------
+// Some callers must not allocate device memory while they run: a process that
+// hands all of the GPU's memory to its own pool at start-up and allows no
+// other allocation, or a latency-bound loop that cannot take the device-wide
+// synchronisation that cudaFree implies.  For them the propagation's scratch
+// (the Q and A blocks, the ln|R_jj| accumulators and the interpolation
+// weights) is one fixed-size array in the library's device image: every GPU
+// that loads the library holds its 4.5 MiB until the process exits.  All calls
+// share it and it keeps the last call's contents, so each call sets Q and the
+// accumulators before use, and calls that overlap on the GPU race on it.
+
+namespace {
+
+constexpr size_t kNoallocQ = FSE_NOALLOC_MAX_QH;   // doubles of Q (and of A)
+constexpr size_t kNoallocAcc = 64;                  // ln|R_jj| accumulators (h <= 64)
+constexpr size_t kNoallocW = FSE_NOALLOC_MAX_N;     // interpolation weights (one per trajectory)
+
+// In host code this name is only a stand-in for the symbol, never a device
+// address: the address is looked up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_lyap_scratch[2 * kNoallocQ + kNoallocAcc + kNoallocW];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_dev[kMaxDevices] = {};   // device address of g_lyap_scratch, per device ordinal
+
+// Q = [I_h; 0] (m x h, row-major) and acc = 0
+__global__ void k_lyap_init(int m, int h, double* Q, double* acc) {
+    const size_t total = (size_t)m * h;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(x / h), col = (int)(x % h);
+        Q[x] = (i == col) ? 1.0 : 0.0;
+        if (x < (size_t)h) acc[x] = 0.0;
+    }
+}
+
+}  // namespace
+
+namespace fse {
+
+// Device address of the static scratch on `device` (which must be current);
+// looked up on the first call per device and cached.
+static int noalloc_scratch(fse_ctx* c, double** out) {
+    if (c->device < 0 || c->device >= kMaxDevices) {
+        c->err = "static scratch: device ordinal out of range";
+        return FSE_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[c->device]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_lyap_scratch);
+        if (e != cudaSuccess || !ptr) {
+            c->err = std::string("static scratch: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+            return FSE_ECUDA;
+        }
+        g_scratch_dev[c->device] = (double*)ptr;
+    }
+    *out = g_scratch_dev[c->device];
+    return FSE_OK;
+}
+
+int lyapunov_run_noalloc(fse_ctx* c, double w, int N_Ly, int h, double* sigma) {
+    const Params& p = c->p;
+    const int m = 2 * p.n;
+    if (h < 1 || (size_t)h > kNoallocAcc || (size_t)m * h > kNoallocQ || (size_t)p.N > kNoallocW) {
+        c->err = "static scratch: size beyond its maximum";
+        return FSE_EINVAL;
+    }
+    double* base = nullptr;
+    const int rc = noalloc_scratch(c, &base);
+    if (rc) return rc;
+    double* Q = base;
+    double* A = base + kNoallocQ;
+    double* acc = base + 2 * kNoallocQ;
+    double* wts = acc + kNoallocAcc;
+    k_lyap_init<<<nblocks((size_t)m * h, 256), 256, 0, c->stream>>>(m, h, Q, acc);
+    const size_t warps = (size_t)m * h;
+    const int g = (int)((warps * 32 + 255) / 256);
+    for (int i = 1; i <= N_Ly; ++i) {
+        double ph[3] = {0, 0, 0};
+        for (int j = 0; j < p.d - 1; ++j) ph[j] = 2.0 * (i - 1) * M_PI * c->rho[j];
+        k_lyap_weights<<<nblocks(p.N, 128), 128, 0, c->stream>>>(p.N, p.U, p.d - 1, c->d.ktab, c->d.Gi,
+                                                             ph[0], ph[1], ph[2], wts);
+        if (p.prec == FSE_MIXED_FP32)
+            k_lyap_prop<float><<<g, 256, 0, c->stream>>>(p.N, p.n, p.ld, h, w, (const float*)c->d.X,
+                                                        (const float*)c->d.V, wts, Q, A);
+        else
+            k_lyap_prop<double><<<g, 256, 0, c->stream>>>(p.N, p.n, p.ld, h, w, (const double*)c->d.X,
+                                                         (const double*)c->d.V, wts, Q, A);
+        k_lyap_qr<<<1, 512, 0, c->stream>>>(m, h, A, Q, acc);
+    }
+    double hacc[kNoallocAcc];
+    cudaMemcpyAsync(hacc, acc, sizeof(double) * h, cudaMemcpyDeviceToHost, c->stream);
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("static-scratch Lyapunov run: ") + cudaGetErrorString(e);
+        return FSE_ECUDA;
+    }
     const double T1 = 2.0 * M_PI / w;
     for (int j = 0; j < h; ++j) sigma[j] = hacc[j] / (N_Ly * T1);
     return FSE_OK;

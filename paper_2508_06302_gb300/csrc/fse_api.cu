@@ -711,6 +711,25 @@ extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, in
     return rc ? rc : st;
 }
 
+extern "C" int fse_lyapunov_noalloc(fse_ctx* c, const double* Z0, double w, int N_Ly, int h, double* sigma) {
+    if (!c || !Z0 || !sigma) return FSE_EINVAL;
+    if (N_Ly < 1 || h < 1 || h > 64 || h > 2 * c->p.n)
+        return set_err(c, FSE_EINVAL, "need N_Ly >= 1, 1 <= h <= min(64, 2n)");
+    if ((size_t)2 * c->p.n * h > FSE_NOALLOC_MAX_QH)
+        return set_err(c, FSE_EINVAL, "2 n h exceeds FSE_NOALLOC_MAX_QH of the static scratch (262144 doubles)");
+    if (c->p.N > FSE_NOALLOC_MAX_N)
+        return set_err(c, FSE_EINVAL, "number of trajectories exceeds FSE_NOALLOC_MAX_N of the static scratch (65536)");
+    cudaSetDevice(c->device);
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    cudaMemcpyAsync(c->d.Z0, Z0, m * 8, cudaMemcpyHostToDevice, c->stream);
+    int rc = run_eval(c, c->d.Z0, w, c->d.R, 1);
+    if (rc) return rc;
+    const int st = collect_status(c, nullptr, nullptr);
+    if (st < 0 && st != FSE_ENOCONV) return st;
+    rc = fse::lyapunov_run_noalloc(c, w, N_Ly, h, sigma);
+    return rc ? rc : st;
+}
+
 extern "C" int fse_set_steps(fse_ctx* c, int n_steps) {
     if (!c || n_steps < 0) return FSE_EINVAL;
     c->n_steps = n_steps;

@@ -159,6 +159,8 @@ void launch_phi_copy(fse_ctx* c, double* Phi_dev, double* dzdw_dev);
 void launch_dense_jac(fse_ctx* c, double* J);
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
+// same propagation with the static device scratch of fse_aft.cu (no allocation)
+int lyapunov_run_noalloc(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
 
 // vector helpers on the context stream (fse_aft.cu)
 void vec_axpby(fse_ctx* c, size_t n, double a, const double* x, double b, double* y);

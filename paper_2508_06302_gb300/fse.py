@@ -88,6 +88,7 @@ def load(path: Optional[str] = None):
         "fse_monodromy": (ctypes.c_int, [_VP, _DP, _DP]),
         "fse_newton_step": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP]),
         "fse_lyapunov": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
+        "fse_lyapunov_noalloc": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
         "fse_timings": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
         "fse_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
         "fse_set_steps": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -275,6 +276,15 @@ class Context:
         Z = np.ascontiguousarray(Z0, dtype=np.float64)
         out = np.zeros(h)
         rc = load().fse_lyapunov(self.h, _dp(Z), float(omega1), int(N_Ly), int(h), _dp(out))
+        self._check(rc, (FSE_ENOCONV,))
+        return out
+
+    def lyapunov_noalloc(self, Z0, omega1, N_Ly, h):
+        """fse_lyapunov_noalloc: the exponents of `lyapunov` with no device
+        allocation (static library scratch shared by every call)."""
+        Z = np.ascontiguousarray(Z0, dtype=np.float64)
+        out = np.zeros(h)
+        rc = load().fse_lyapunov_noalloc(self.h, _dp(Z), float(omega1), int(N_Ly), int(h), _dp(out))
         self._check(rc, (FSE_ENOCONV,))
         return out
 
