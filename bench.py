@@ -41,6 +41,10 @@ def parse():
                     help="Newmark steps of the plain FP64 form timed for the comparison line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traj", type=int, default=0,
+                    help="small case: N trajectories (H = (N-1)//2) instead of the workload's")
+    ap.add_argument("--newmark-steps", type=int, default=0,
+                    help="small case: integrate only the first K Newmark steps of the period")
     return ap.parse_args()
 
 
@@ -140,8 +144,58 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def band_nnz(A):
-    return int(np.count_nonzero(A))
+def csr_counts(m):
+    """Nonzeros of the union pattern of M, D, K and of the K_t pattern of the nonlinear elements."""
+    nnz = int(np.count_nonzero((m.M != 0) | (m.D != 0) | (m.K != 0)))
+    kt = set()
+    for e in range(m.n_nl):
+        dofs = [int(x) for x in m.nl_dof[e] if x >= 0]
+        for a in dofs:
+            for b2 in dofs:
+                kt.add((a, b2))
+    return nnz, len(kt)
+
+
+def step_work(m, N, band, ld, prec_bytes):
+    """Algorithmic FP32 flops and HBM bytes per launch (all N trajectories, one Newmark step)
+    of the three sensitivity kernels:
+      rhs  Y = (A - K_t(q_k)) X_k + B V_k on the CSR patterns: 2 (2 nnz + nnz_kt) P flops,
+           reads X, V and writes Y: 3 n P words;
+      fwd  L Y' = Y (band b): 2 (n b - b (b + 1) / 2) P flops, reads Y and writes Y': 2 n P words;
+      bwd  L^T X_{k+1} = Y' and V_{k+1} = 2/D (X_{k+1} - X_k) - V_k: the same flops + 3 n P,
+           reads Y', X_k, V_k and writes X_{k+1}, V_{k+1}: 5 n P words.
+    P = 2n + 1 tangent columns; the padding columns (P..ld) are not counted."""
+    n, P, b = m.n, 2 * m.n + 1, band
+    nnz, nnz_kt = csr_counts(m)
+    tri = n * b - b * (b + 1) / 2
+    w = prec_bytes
+    return {
+        "sens_rhs": (2.0 * (2 * nnz + nnz_kt) * P * N, 3.0 * n * P * w * N),
+        "sens_fwd": (2.0 * tri * P * N, 2.0 * n * P * w * N),
+        "sens_bwd": ((2.0 * tri + 3.0 * n) * P * N, 5.0 * n * P * w * N),
+    }
+
+
+def recorded_traffic(kernel, workload_name):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/, with the hash of the
+    kernel sources it was taken on; None when absent or when the sources changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload_name))
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
+            rec[k.strip()] = v.strip().strip("`")
+    src = os.path.join(ROOT, "paper_2508_06302_gb300", "csrc", "fse_sens.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("sources_sha256_16") != h:
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
 
 
 def cpu_baseline(wl, seconds):
@@ -209,11 +263,19 @@ def main():
     torch.cuda.set_device(local)
     from paper_2508_06302_gb300 import fse
     wl = workload(args.workload)
+    if args.traj > 0:
+        import dataclasses
+        wl = dataclasses.replace(wl, S=[args.traj], H=[(args.traj - 1) // 2],
+                                 name=wl.name + "_N%d" % args.traj)
     m = wl.model
     # every rank runs its own continuation point (weak scaling, no exchange)
     w1 = wl.omega1 * (1.0 + 0.01 * rank)
     ctx = fse.Context.from_workload(wl, precision=args.precision, device=local)
     ctx.profile(True)
+    n_newmark = wl.S1
+    if 0 < args.newmark_steps < wl.S1:
+        n_newmark = args.newmark_steps
+        ctx.set_steps(n_newmark)
     nu = ctx.n_unknowns
     Z = torch.tensor(initial_coeffs(wl), dtype=torch.float64, device="cuda")
     R = torch.zeros(nu, dtype=torch.float64, device="cuda")
@@ -233,7 +295,7 @@ def main():
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    phase = np.zeros(5)
+    phase = np.zeros(6)
     e0.record()
     for _ in range(args.steps):
         step()
@@ -248,16 +310,17 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
         torch.distributed.barrier()
-    traj_steps = wl.N * wl.S1
+    traj_steps = wl.N * n_newmark
     value = traj_steps * world / (ms / 1e3)
-    phase /= args.steps
+    phase /= args.steps                 # per step; phase[5] is the mean refactor count
 
     # end-to-end through the host-pointer API (H2D of Z(0), D2H of R inside the timed region)
     Zh = initial_coeffs(wl)
     t0 = time.perf_counter()
-    for _ in range(max(1, args.steps // 2)):
+    n_e2e = max(1, args.steps // 2)
+    for _ in range(n_e2e):
         Rh, st_h, it_h, rc_h = ctx.residual_jacobian(Zh, w1, True)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps // 2)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
 
     # plain FP64 form of the same workload, timed on its first --fp64-steps Newmark steps
     fp64 = None
@@ -279,26 +342,46 @@ def main():
         c64_short.close()
 
     peaks, src = measured_peaks()
-    # dominant kernel and its roofline (FP32 SIMT arithmetic: alu bound)
+    # per-kernel rooflines of the sensitivity kernels (FP32 SIMT arithmetic or HBM, whichever
+    # bounds the kernel) from their event-timed average launch duration on the launching stream
     names = ["state", "sens_rhs", "sens_fwd", "sens_bwd"]
-    k = int(np.argmax(phase[1:5]))
-    nnzMD = band_nnz(m.M) + band_nnz(m.D)
     b = ctx.band
-    n, P, N = m.n, 2 * m.n + 1, wl.N
-    # algorithmic flops per step (one launch) of each sensitivity kernel
-    flops = {"sens_rhs": 2.0 * nnzMD * P * N,
-             "sens_fwd": 2.0 * (n * b - b * (b + 1) / 2) * P * N,
-             "sens_bwd": 2.0 * (n * b - b * (b + 1) / 2) * P * N + 6.0 * n * P * N}
+    n, N = m.n, wl.N
+    wb = 4 if args.precision == "mixed_fp32" else 8
+    work = step_work(m, N, b, 0, wb)
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12        # TFLOP/s of the FP32 SIMT pipes
+    lanes = 128 if wb == 4 else 2            # FP32 / FP64 SIMT lanes per SM (FP64: 1/64 of FP32)
+    alu_peak = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kernels = {}
+    for k_i, kname in enumerate(names):
+        if kname not in work:
+            continue
+        avg_ms = phase[1 + k_i] / n_newmark
+        if avg_ms <= 0:
+            continue
+        fl, by = work[kname]
+        t_alu = fl / (alu_peak * 1e12)
+        t_hbm = by / (hbm_peak * 1e9)
+        if t_alu >= t_hbm:
+            ach = fl / (avg_ms / 1e3) / 1e12
+            kernels[kname] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                              "frac": ach / alu_peak, "avg_launch_ms": avg_ms,
+                              "algorithmic_flops": fl, "algorithmic_bytes": by}
+        else:
+            ach = by / (avg_ms / 1e3) / 1e9
+            kernels[kname] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": ach / hbm_peak, "avg_launch_ms": avg_ms,
+                              "algorithmic_flops": fl, "algorithmic_bytes": by}
     roof = None
-    kname = names[k]
-    if kname in flops:
-        avg_ms = phase[1 + k] / wl.S1
-        ach = flops[kname] / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % sm_mhz}
+    if kernels:
+        kname = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
+        kk = kernels[kname]
+        roof = {"kernel": kname, "bound": kk["bound"], "achieved": kk["achieved"], "peak": kk["peak"],
+                "unit": kk["unit"], "frac": kk["frac"],
+                "traffic": recorded_traffic("k_" + kname, wl.name),
+                "peak_source": ("%s of %s (HBM copy)" % (hbm_peak, src)) if kk["bound"] == "hbm" else
+                ("152 SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (lanes, sm_mhz))}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, args.cpu_seconds)
@@ -307,14 +390,19 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 state / f32 sensitivities", "data": "synthetic",
         "config": {"workload": wl.name, "n": n, "N": N, "H": wl.H, "S1": wl.S1, "band": b,
+                   "newmark_steps_timed": n_newmark,
                    "precision": args.precision, "l2": "working set >> L2 (no flush needed)"},
-        "status": int(rc), "newton_iters_per_step": float(np.mean(its)) / wl.S1,
-        "phase_ms": {nm: float(v) for nm, v in zip(["total"] + names, phase)},
+        "status": int(rc), "newton_iters_per_step": float(np.mean(its)) / n_newmark,
+        "phase_ms": {nm: float(v) for nm, v in zip(["total"] + names, phase[:5])},
+        "refactors_per_traj_step": float(phase[5]),
+        "kernels": kernels,
         "e2e": {"value": traj_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nu * 8,
                 "d2h_bytes_per_step": nu * 8 + 8 * N},
         "fp64_plain": fp64,
         "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
-        "gpu_launches": 3 + wl.S1 * 4 + 4,
+        # per evaluation: i-DFT, split, initial state, tangent init, S1 x (state step + the three
+        # sensitivity kernels), join, DFT + residual
+        "gpu_launches": args.steps * (4 * n_newmark + 6),
         "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "peaks_source": src,
     }
     if rank == 0:
