@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -64,15 +65,62 @@ static cudaError_t dalloc(P** p, size_t bytes) {
     return cudaMalloc((void**)p, bytes > 0 ? bytes : 16);
 }
 
+// Row groups of the right-hand-side kernel: rows whose column patterns are identical and
+// at most 7 rows apart (the dofs of one FE node that couple to the same neighbours), at most
+// R rows per group.  Entries of a group are the common pattern; map holds the CSR index of
+// every (entry, row) pair.
+struct RowGroups {
+    int R = 1;
+    std::vector<int> rows;   // ng x R, -1 = padding
+    std::vector<int> ptr;    // ng + 1
+    std::vector<int> col;    // E
+    std::vector<int> map;    // E x R
+};
+
+static RowGroups group_rows(int n, const std::vector<int>& cptr, const std::vector<int>& ccol, int R) {
+    RowGroups G;
+    G.R = R;
+    std::map<std::vector<int>, int> open;
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < n; ++i) {
+        std::vector<int> pat(ccol.begin() + cptr[i], ccol.begin() + cptr[i + 1]);
+        auto it = open.find(pat);
+        if (it != open.end()) {
+            std::vector<int>& mem = members[it->second];
+            if ((int)mem.size() < R && i - mem[0] < 8) {
+                mem.push_back(i);
+                continue;
+            }
+        }
+        open[pat] = (int)members.size();
+        members.push_back({i});
+    }
+    G.ptr.push_back(0);
+    for (const auto& mem : members) {
+        const int i0 = mem[0], len = cptr[i0 + 1] - cptr[i0];
+        for (int r = 0; r < R; ++r) G.rows.push_back(r < (int)mem.size() ? mem[r] : -1);
+        for (int k = 0; k < len; ++k) {
+            G.col.push_back(ccol[cptr[i0] + k]);
+            for (int r = 0; r < R; ++r) G.map.push_back(r < (int)mem.size() ? cptr[mem[r]] + k : -1);
+        }
+        G.ptr.push_back((int)G.col.size());
+    }
+    return G;
+}
+
+// bytes of one group record: the ring slot (int, padded to 8 bytes), then 2R values
+static int group_record_bytes(int R, size_t tsz) { return (int)((8 + 2 * R * tsz + 15) / 16 * 16); }
+
 static void free_ctx(fse_ctx* c) {
     if (!c) return;
     void* ptrs[] = {c->d.Mb, c->d.F, c->d.el_type, c->d.el_dof, c->d.el_p, c->d.col_off,
-                    c->d.cs_ptr, c->d.cs_col, c->d.cs_slot, c->d.kt_slot, c->d.cs_m, c->d.cs_d, c->d.cs_k, c->d.cs_s, c->d.cs_A,
+                    c->d.cs_ptr, c->d.cs_col, c->d.kt_slot, c->d.g_pass, c->d.g_info, c->d.g_rr, c->d.g_map, c->d.g_slot,
+                    c->d.g_rec, c->d.cs_m, c->d.cs_d, c->d.cs_k, c->d.cs_s, c->d.cs_A,
                     c->d.cs_B, c->d.kt_ptr, c->d.kt_col, c->d.kt_soff, c->d.kt_src, c->d.ke,
                     c->d.kt_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
                     c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
                     c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
-                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->Jd, c->piv};
+                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -284,11 +332,93 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.nnz_kt = (int)kcol.size();
     p.nblk = (n + FSE_BLK - 1) / FSE_BLK;
     p.ld = (p.P + 3) & ~3;
-    p.RW = 2 * b + 2 * FSE_RHS_G;
+    // row groups: R chosen by the shared-memory wavefronts per 64-column pass of an entry
+    // (4 for the X and V elements, RB / 16 for the broadcast record)
+    RowGroups grp;
+    {
+        double best = 0.0;
+        for (int R = 1; R <= FSE_RHS_MAXR; ++R) {
+            RowGroups cand = group_rows(n, cptr, ccol, R);
+            const double cost = (double)cand.col.size() * (4.0 + group_record_bytes(R, tsz) / 16.0);
+            if (R == 1 || cost < best) {
+                best = cost;
+                grp = std::move(cand);
+            }
+        }
+    }
+    p.R = grp.R;
+    p.ng = (int)grp.ptr.size() - 1;
+    p.nE = (int)grp.col.size();
+    p.RB = group_record_bytes(p.R, tsz);
+    // per pass of FSE_RHS_GPS groups: rows that must be staged (monotone), entries, ring span
+    const int npass = (p.ng + FSE_RHS_GPS - 1) / FSE_RHS_GPS;
+    std::vector<int> ghi(npass), gmin(npass);
+    {
+        int hi = 0;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int g0 = ps * FSE_RHS_GPS, g1 = std::min(p.ng, g0 + FSE_RHS_GPS);
+            int mx = 0;
+            for (int g = g0; g < g1; ++g)
+                for (int r = 0; r < p.R; ++r) mx = std::max(mx, grp.rows[(size_t)g * p.R + r]);
+            hi = std::max(hi, std::min(n, mx + b + 1));
+            ghi[ps] = hi;
+            gmin[ps] = grp.rows[(size_t)g0 * p.R];
+            p.ME = std::max(p.ME, grp.ptr[g1] - grp.ptr[g0]);
+        }
+        // rows are staged in 32-row TMA boxes: the ring (a multiple of 32 rows) holds from the
+        // first row a pass reads up to the last box staged for the passes in flight
+        const int dep = p.prec == FSE_MIXED_FP32 ? FSE_RHS_DEPTH_F32 : FSE_RHS_DEPTH_F64;
+        p.RW = 32;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int top = (ghi[std::min(ps + dep, npass - 1)] + 31) & ~31;
+            p.RW = std::max(p.RW, top - std::max(0, gmin[ps] - b));
+        }
+        p.RW = (p.RW + 31) & ~31;
+    }
     p.RWT = 1;
     while (p.RWT < b + FSE_BLK) p.RWT <<= 1;
-    std::vector<int> cslot(ccol.size()), kslot(kcol.size());
-    for (size_t q = 0; q < ccol.size(); ++q) cslot[q] = ccol[q] % p.RW;
+    // per pass: {rows to stage, first entry, end entry, first K_t entry}, {K_t entries, first
+    // group, 0, 0}; the K_t slice of a pass starts at a multiple of 4 and has a multiple of 4
+    // entries (16-byte bulk copies); per group: {first entry relative to its pass, entries};
+    // per row: {row, K_t begin, K_t end (relative to the pass's slice), 0}
+    p.kt_ld = std::max(4, (p.nnz_kt + 3) & ~3);
+    std::vector<int> gpass((size_t)8 * npass, 0), ginfo((size_t)2 * ((p.ng + 1) & ~1), 0);
+    std::vector<int> grr((size_t)p.ng * p.R * 4, 0);
+    p.MK = 0;
+    for (int ps = 0; ps < npass; ++ps) {
+        const int g0 = ps * FSE_RHS_GPS, g1 = std::min(p.ng, g0 + FSE_RHS_GPS);
+        int k0 = p.nnz_kt, k1 = 0;
+        for (int g = g0; g < g1; ++g)
+            for (int r = 0; r < p.R; ++r) {
+                const int i = grp.rows[(size_t)g * p.R + r];
+                if (i < 0) continue;
+                k0 = std::min(k0, kptr[i]);
+                k1 = std::max(k1, kptr[i + 1]);
+            }
+        const int kb = k1 > k0 ? (k0 & ~3) : 0;
+        const int kn = k1 > k0 ? ((k1 - kb + 3) & ~3) : 0;
+        p.MK = std::max(p.MK, kn);
+        int* d = &gpass[(size_t)8 * ps];
+        d[0] = ghi[ps];
+        d[1] = grp.ptr[g0];
+        d[2] = grp.ptr[g1];
+        d[3] = kb;
+        d[4] = kn;
+        d[5] = g0;
+        for (int g = g0; g < g1; ++g) {
+            ginfo[(size_t)2 * g] = grp.ptr[g] - grp.ptr[g0];
+            ginfo[(size_t)2 * g + 1] = grp.ptr[g + 1] - grp.ptr[g];
+            for (int r = 0; r < p.R; ++r) {
+                const size_t q = (size_t)g * p.R + r;
+                const int i = grp.rows[q];
+                grr[4 * q] = i;
+                grr[4 * q + 1] = i >= 0 ? kptr[i] - kb : 0;
+                grr[4 * q + 2] = i >= 0 ? kptr[i + 1] - kb : 0;
+            }
+        }
+    }
+    std::vector<int> gslot(grp.col.size()), kslot(p.kt_ld, 0);
+    for (size_t q = 0; q < grp.col.size(); ++q) gslot[q] = grp.col[q] % p.RW;
     for (size_t q = 0; q < kcol.size(); ++q) kslot[q] = kcol[q] % p.RW;
     p.smem_state = fse::state_smem(p);
     p.smem_rhs = fse::rhs_smem(p);
@@ -302,7 +432,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     // device allocations
     const size_t Nn = (size_t)N * n, band = (size_t)fb * n, lb = (size_t)n * nb;
     const size_t sensz = (size_t)N * n * p.ld * tsz;
-    const size_t ktsz = (size_t)N * std::max(1, p.nnz_kt) * tsz;
+    const size_t ktsz = (size_t)N * p.kt_ld * tsz;
     const size_t dsz = (size_t)N * p.nblk * FSE_BLK * FSE_BLK * tsz;
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** ptr, size_t bytes) {
@@ -316,8 +446,13 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     A(&c->d.col_off, (size_t)(ncol + 1) * 4);
     A(&c->d.cs_ptr, (size_t)(n + 1) * 4);
     A(&c->d.cs_col, (size_t)p.nnz * 4);
-    A(&c->d.cs_slot, (size_t)p.nnz * 4);
-    A(&c->d.kt_slot, (size_t)std::max(1, p.nnz_kt) * 4);
+    A(&c->d.g_pass, gpass.size() * 4);
+    A(&c->d.g_info, ginfo.size() * 4);
+    A(&c->d.g_rr, (size_t)p.ng * p.R * 16);
+    A(&c->d.g_map, (size_t)p.nE * p.R * 4);
+    A(&c->d.g_slot, (size_t)p.nE * 4);
+    A(&c->d.g_rec, (size_t)p.nE * p.RB);
+    A(&c->d.kt_slot, (size_t)p.kt_ld * 4);
     A(&c->d.cs_m, (size_t)p.nnz * 8);
     A(&c->d.cs_d, (size_t)p.nnz * 8);
     A(&c->d.cs_k, (size_t)p.nnz * 8);
@@ -361,6 +496,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     A(&c->d.status, (size_t)N * 4);
     A(&c->d.iters, (size_t)N * 4);
     A(&c->d.nref, (size_t)N * 4);
+    A(&c->d.flag, 16);
     if (e != cudaSuccess) {
         rc = cuda_check(c, e, "device allocation");
         g_setup_err = c->err;
@@ -378,8 +514,13 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     cudaMemcpyAsync(c->d.col_off, coff.data(), coff.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_ptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_col, ccol.data(), ccol.size() * 4, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->d.cs_slot, cslot.data(), cslot.size() * 4, cudaMemcpyHostToDevice, st);
-    if (p.nnz_kt > 0) cudaMemcpyAsync(c->d.kt_slot, kslot.data(), kslot.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.g_pass, gpass.data(), gpass.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.g_info, ginfo.data(), ginfo.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.g_rr, grr.data(), grr.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.g_map, grp.map.data(), grp.map.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.g_slot, gslot.data(), gslot.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d.kt_slot, kslot.data(), kslot.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(c->d.kt_val, 0, FSE_NBUF_KT * ktsz, st);
     cudaMemcpyAsync(c->d.cs_m, cm.data(), cm.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_d, cd.data(), cd.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_k, ck.data(), ck.size() * 8, cudaMemcpyHostToDevice, st);
@@ -396,6 +537,13 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     cudaMemsetAsync(c->d.status, 0, (size_t)N * 4, st);
     cudaMemsetAsync(c->d.iters, 0, (size_t)N * 4, st);
     cudaMemsetAsync(c->d.nref, 0, (size_t)N * 4, st);
+    cudaMemsetAsync(c->d.flag, 0, 16, st);
+    if (fse::make_tangent_maps(c) != FSE_OK) {
+        rc = set_err(c, FSE_ECUDA, "TMA descriptor encoding failed");
+        g_setup_err = c->err;
+        free_ctx(c);
+        return rc;
+    }
     fse::launch_fill_tables(c);
     const int bad = fse::launch_factor_M(c);
     rc = cuda_check(c, cudaStreamSynchronize(st), "setup");
@@ -444,6 +592,7 @@ static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, i
     const Params& p = c->p;
     if (w != c->omega_S) {
         fse::launch_build_ops(c, w);
+        fse::launch_build_groups(c);
         c->omega_S = w;
     }
     const int steps = (c->n_steps > 0 && c->n_steps < p.S1) ? c->n_steps : p.S1;
@@ -503,10 +652,16 @@ static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, i
 static int collect_status(fse_ctx* c, int* ts, int* it) {
     const int N = c->p.N;
     std::vector<int> st(N), its(N);
+    int flag = 0;
     cudaMemcpyAsync(st.data(), c->d.status, N * 4, cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(its.data(), c->d.iters, N * 4, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&flag, c->d.flag, 4, cudaMemcpyDeviceToHost, c->stream);
     int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "evaluation");
     if (rc) return rc;
+    if (flag) {
+        cudaMemsetAsync(c->d.flag, 0, 4, c->stream);
+        return set_err(c, FSE_ECUDA, "a pipeline wait of the tangent kernels timed out");
+    }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) c->timing[0] = ms;
     if (c->prof_pending) {

@@ -1,6 +1,7 @@
 // Internal declarations of the FSE-Shooting CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (types only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 #include <string>
@@ -12,7 +13,11 @@
 #define FSE_BLK 32        // row block of the blocked triangular solves
 #define FSE_NBUF_F 2      // factor buffers (step parity)
 #define FSE_NBUF_KT 3     // tangent-value buffers (step index mod 3)
-#define FSE_RHS_G 16      // rows per step of the right-hand-side kernel (2 per warp)
+#define FSE_RHS_GPS 16    // row groups per pass of the right-hand-side kernel (one per warp)
+#define FSE_RHS_MAXR 4    // rows per group of the right-hand-side kernel, at most
+// passes of the right-hand-side kernel in flight ahead of the one computed (FP32 / FP64 tangents)
+#define FSE_RHS_DEPTH_F32 3
+#define FSE_RHS_DEPTH_F64 2
 #define FSE_MAX_BAND 224  // half-bandwidth limit of the blocked solves
 
 namespace fse {
@@ -41,7 +46,6 @@ struct Dev {
     // CSR of the union pattern of M, D, K
     int* cs_ptr = nullptr;
     int* cs_col = nullptr;
-    int* cs_slot = nullptr;  // cs_col mod RW (ring slot of the right-hand-side kernel)
     double* cs_m = nullptr;
     double* cs_d = nullptr;
     double* cs_k = nullptr;
@@ -52,10 +56,18 @@ struct Dev {
     int* kt_ptr = nullptr;
     int* kt_col = nullptr;
     int* kt_slot = nullptr;  // kt_col mod RW
+    // row groups of the right-hand-side kernel (rows with identical column patterns)
+    int* g_pass = nullptr;   // 8 per pass: rows to stage, entry range, K_t slice (first, count), first group
+    int* g_info = nullptr;   // 2 per group (even count): first entry relative to its pass, entries
+    int* g_rr = nullptr;     // ng x R row records {row, K_t begin, K_t end, 0} (row -1 = padding; the
+                             // K_t range relative to the pass's slice)
+    int* g_map = nullptr;    // E x R CSR index of entry and row (-1 = none)
+    int* g_slot = nullptr;   // E ring slot (column mod RW)
+    void* g_rec = nullptr;   // E records of RB bytes: slot, then A values (R), B values (R)
     int* kt_soff = nullptr;
     int* kt_src = nullptr;   // element * 36 + a * 6 + b
     double* ke = nullptr;    // N x n_el x 36 element tangents (scratch of k_state)
-    void* kt_val = nullptr;  // FSE_NBUF_KT x N x nnz_kt
+    void* kt_val = nullptr;  // FSE_NBUF_KT x N x kt_ld
     void* romega = nullptr;  // 2 x N x n   right-hand side of the w_1 column
     // AFT tables
     double* phis = nullptr;  // N x (d-1)
@@ -92,13 +104,18 @@ struct Dev {
     int* status = nullptr;   // N
     int* iters = nullptr;    // N
     int* nref = nullptr;     // N  in-loop refactorisations of the per-step Newton
+    int* flag = nullptr;     // error flag of the kernels' bounded waits (0 = fine)
 };
 
 struct Params {
     int n = 0, b = 0, d = 0, e = 0, N = 0, U = 0, L = 0, S1 = 0, P = 0;
     int maxit = 0, prec = 0, ncolors = 0, n_el = 0, nnz = 0, nnz_kt = 0, nblk = 0;
     int ld = 0;              // row stride of the tangent arrays: P rounded up to a multiple of 4
-    int RW = 0;              // ring rows of the right-hand-side kernel (2b + 2 FSE_RHS_G)
+    int RW = 0;              // ring rows of the right-hand-side kernel (two passes + 2b)
+    int R = 1, ng = 0, nE = 0, ME = 0, RB = 16;   // row groups: rows per group, groups, entries,
+                                                  // entries per pass (max), record bytes
+    int kt_ld = 4;           // per-trajectory stride of the K_t values (nnz_kt rounded up to 4)
+    int MK = 0;              // K_t entries of a pass's slice (max, a multiple of 4)
     int RWT = 0;             // ring rows of the blocked solves (power of two >= b + 32)
     double tol = 0;
     size_t smem_state = 0, smem_rhs = 0, smem_trsm = 0;
@@ -109,6 +126,8 @@ struct Params {
 struct fse_ctx {
     fse::Params p;
     fse::Dev d;
+    alignas(64) CUtensorMap tmX{};   // TMA maps of the tangent arrays X, V ([N][n][ld], boxes of
+    alignas(64) CUtensorMap tmV{};   // 32 rows x the right-hand-side kernel's column tile)
     int device = 0;
     cudaStream_t stream = nullptr;   // state path + everything ordered
     cudaStream_t stream2 = nullptr;  // sensitivity kernels (overlap with the next state step)
@@ -141,10 +160,14 @@ size_t state_smem(const Params& p);
 size_t rhs_smem(const Params& p);
 size_t trsm_smem(const Params& p);
 
+// TMA maps of X and V for the right-hand-side kernel (after the allocations)
+int make_tangent_maps(fse_ctx* c);
+
 // launchers
 void ensure_constants();
 void launch_fill_tables(fse_ctx* c);
 void launch_build_ops(fse_ctx* c, double omega1);
+void launch_build_groups(fse_ctx* c);
 int launch_factor_M(fse_ctx* c);
 void launch_idft(fse_ctx* c, const double* Z, double* zb);
 void launch_init_state(fse_ctx* c, double omega1);

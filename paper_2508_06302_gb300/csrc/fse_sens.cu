@@ -20,10 +20,12 @@
 namespace fse {
 
 struct SensArgs {
-    int n, b, P, ld, nnz_kt, nblk, RW, RWT;
+    int n, b, P, ld, kt_ld, nblk, RW, RWT;
+    int ng, ME, RB, MK;
     double a2c;
-    const int *cs_ptr, *cs_slot, *kt_ptr, *kt_slot;
-    const void *Aop, *Bop, *kt_val, *romega;
+    const int* kt_slot;
+    int* err;   // set when a pipeline wait gives up
+    const void *g_rec, *g_rr, *g_info, *g_pass, *kt_val, *romega;
     const void *Lc, *Lr, *Dinv;
     void *X, *V, *Y;
 };
@@ -76,106 +78,318 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// ---- mbarrier / bulk-copy helpers (every wait is bounded: after about 2 s of SM clock the
+// waiting thread raises the error flag and gives up)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned tx) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
+                 "r"(tx)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
+    const unsigned a = smem_addr(bar);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1ll << 32)) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 3-D tiled TMA load (box of the tensor map at {x, y, z}) completing on bar; the shared
+// destination is 128-byte aligned and x * element size a multiple of 16 bytes
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// explicit shared-memory loads on 32-bit shared addresses
+__device__ __forceinline__ uint4 lds_u4(unsigned a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int2 lds_i2(unsigned a) {
+    int2 v;
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int lds_i(unsigned a) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];\n" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 lds_f2(unsigned a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_f(unsigned a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double lds_d(unsigned a) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];\n" : "=d"(v) : "r"(a));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T lds_t(unsigned a) {
+    if constexpr (sizeof(T) == 4)
+        return lds_f(a);
+    else
+        return lds_d(a);
+}
+
+// bytes of one group record: the ring slot (int, padded to 8 bytes), then R values of A and
+// R values of B
+template <typename T, int R>
+__host__ __device__ constexpr int rhs_record_bytes() {
+    return (int)((8 + 2 * R * sizeof(T) + 15) / 16 * 16);
+}
 
 // RHS[s][i][t] = sum_j A_ij X[j][t] + B_ij V[j][t] - sum_j K_t(q_k)_ij X[j][t] (+ romega_i at t = 2n).
-// One CTA = all rows of one trajectory for 64 directions.  A ring of RW = 2b + 2G rows of
-// X and V in shared memory holds the rows [i - b, i + b] of the G rows being processed plus
-// the G rows prefetched (cp.async) for the next step, so every tangent row is read from
-// memory once per Newmark step and the loads overlap the arithmetic.
-template <typename T>
-__global__ void __launch_bounds__(256) k_sens_rhs(SensArgs A) {
-    using T2 = typename Vec2<T>::type;
-    constexpr int G = FSE_RHS_G;
-    constexpr int EPC = 16 / sizeof(T);            // elements per 16-byte copy
-    constexpr int CPR = 64 / EPC;                  // copies per row and array
-    const int n = A.n, b = A.b, P = A.P, ld = A.ld, RW = A.RW;
-    const int s = blockIdx.y, t0 = blockIdx.x * 64;
+// One CTA = all rows of one trajectory for CW directions (64 in FP32, 32 in FP64).  Rows go
+// in groups of up to R rows with one common column pattern, one group per consumer warp and
+// FSE_RHS_GPS groups per pass: each X/V element read from shared memory feeds R rows.  A ring
+// of RW rows of X and V in shared memory holds the rows of the passes in flight; a
+// producer warp streams, for the passes ahead, the tangent rows, the group records (slot, A
+// and B values), the group and row records and the pass's slice of K_t(q_k) (slots and
+// values) with bulk copies that complete on a "full" mbarrier per buffer, and refills a
+// buffer once all consumer warps have arrived on its "empty" mbarrier.  Every tangent row is
+// read from memory once per step; the consumers read nothing else from global memory.
+template <typename T, int R>
+__global__ void __launch_bounds__(32 * (FSE_RHS_GPS + 1), 1)
+    k_sens_rhs(SensArgs A, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV) {
+    constexpr int CW = sizeof(T) == 4 ? 64 : 32;   // columns per CTA
+    constexpr int EL = CW / 32;                     // columns per lane
+    constexpr int GPS = FSE_RHS_GPS;
+    constexpr int NB = (sizeof(T) == 4 ? FSE_RHS_DEPTH_F32 : FSE_RHS_DEPTH_F64) + 1;   // buffers in flight
+    constexpr int RB = rhs_record_bytes<T, R>();
+    constexpr int RW4 = RB / 4;                     // 32-bit words per record
+    const int n = A.n, P = A.P, ld = A.ld, RW = A.RW, ng = A.ng, ME = A.ME, MK = A.MK;
+    const int s = blockIdx.y, t0 = blockIdx.x * CW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ __align__(8) unsigned long long bar_full[NB], bar_empty[NB];
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* rX = reinterpret_cast<T*>(smraw);        // RW x 64
-    T* rV = rX + (size_t)RW * 64;
+    // per buffer: group records ME x RB | row records GPS x R int4 | group entry ranges GPS int2 |
+    // K_t slots MK int | K_t values MK T
+    const size_t bufsz = (size_t)ME * RB + (size_t)GPS * R * 16 + (size_t)GPS * 8 + (size_t)MK * (4 + sizeof(T));
+    unsigned char* sm128 = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);   // TMA boxes: 128-byte aligned
+    T* rX = reinterpret_cast<T*>(sm128);            // RW x CW (RW a multiple of 32)
+    T* rV = rX + (size_t)RW * CW;
+    unsigned char* bufs = reinterpret_cast<unsigned char*>(rV + (size_t)RW * CW);
     const size_t base = (size_t)s * n * ld;
-    const T* X = reinterpret_cast<const T*>(A.X) + base;
-    const T* V = reinterpret_cast<const T*>(A.V) + base;
     T* Y = reinterpret_cast<T*>(A.Y) + base;
-    const T* Aop = reinterpret_cast<const T*>(A.Aop);
-    const T* Bop = reinterpret_cast<const T*>(A.Bop);
-    const T* ktv = reinterpret_cast<const T*>(A.kt_val) + (size_t)s * A.nnz_kt;
-    const T* rom = reinterpret_cast<const T*>(A.romega) + (size_t)s * n;
-    // issue the copies of rows [r0, r1) into their ring slots
-    auto fill = [&](int r0, int r1) {
-        const int cnt = (r1 - r0) * CPR;
-        for (int idx = threadIdx.x; idx < 2 * cnt; idx += blockDim.x) {
-            const int arr = idx >= cnt;
-            const int q = arr ? idx - cnt : idx;
-            const int r = r0 + q / CPR, c = (q % CPR) * EPC, t = t0 + c;
-            const T* src = (arr ? V : X) + (size_t)r * ld + (t < ld ? t : 0);
-            T* dst = (arr ? rV : rX) + (size_t)(r % RW) * 64 + c;
-            cp_async16(dst, src, t < ld ? 16 : 0);
+    const int npass = (ng + GPS - 1) / GPS;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NB; ++k) {
+            mbar_init(&bar_full[k], 1);
+            mbar_init(&bar_empty[k], GPS);
         }
-    };
-    int loaded = min(n, G + b);
-    fill(0, loaded);
-    cp_async_commit();
-    for (int g0 = 0; g0 < n; g0 += G) {
-        const int need = min(n, g0 + 2 * G + b);      // rows of the next step
-        if (need > loaded) fill(loaded, need);
-        loaded = max(loaded, need);
-        cp_async_commit();
-        cp_async_wait1();                                 // this step's rows have landed
-        __syncthreads();
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == GPS) {
+        // ---- producer
+        const unsigned char* rec = reinterpret_cast<const unsigned char*>(A.g_rec);
+        const int4* rr_g = reinterpret_cast<const int4*>(A.g_rr);
+        const int2* gi_g = reinterpret_cast<const int2*>(A.g_info);
+        const int4* pd = reinterpret_cast<const int4*>(A.g_pass);
+        const T* ktv = reinterpret_cast<const T*>(A.kt_val) + (size_t)s * A.kt_ld;
+        constexpr unsigned chunkbytes = 32u * CW * (unsigned)sizeof(T);   // one TMA box: 32 rows
+        int loadedc = 0, q = 0;                                            // 32-row chunks staged
+        int4 d0 = pd[0], d1 = pd[1];
+        for (; q < npass; ++q) {
+            const int slot = q % NB;
+            int4 n0 = d0, n1 = d1;
+            if (q + 1 < npass) {
+                n0 = pd[2 * q + 2];
+                n1 = pd[2 * q + 3];
+            }
+            if (q >= NB && !mbar_wait(&bar_empty[slot], ((q / NB) - 1) & 1, A.err)) break;
+            const int need = d0.x, e0 = d0.y, e1 = d0.z, kb = d0.w, kn = d1.x, g0 = d1.y;
+            const int g1 = min(ng, g0 + GPS);
+            const int nch = max(0, ((need + 31) >> 5) - loadedc);
+            const unsigned mbytes = (unsigned)((e1 - e0) * RB), rbytes = (unsigned)((g1 - g0) * R * 16);
+            const unsigned ibytes = (unsigned)(((g1 - g0 + 1) / 2) * 16);
+            const unsigned kbytes = (unsigned)(kn * (4 + sizeof(T)));
+            unsigned char* buf = bufs + (size_t)slot * bufsz;
+            if (lane == 0) mbar_arrive_tx(&bar_full[slot], 2u * nch * chunkbytes + mbytes + rbytes + ibytes + kbytes);
+            __syncwarp();
+            for (int k = lane; k < 2 * nch; k += 32) {
+                const int arr = k & 1, r0 = 32 * (loadedc + (k >> 1));
+                tma_load3((arr ? rV : rX) + (size_t)(r0 % RW) * CW, arr ? &tmV : &tmX, t0, r0, s, &bar_full[slot]);
+            }
+            if (lane == 0) {
+                unsigned char* b2 = buf;
+                bulk_g2s(b2, rec + (size_t)e0 * RB, mbytes, &bar_full[slot]);
+                b2 += (size_t)ME * RB;
+                bulk_g2s(b2, rr_g + (size_t)g0 * R, rbytes, &bar_full[slot]);
+                b2 += (size_t)GPS * R * 16;
+                bulk_g2s(b2, gi_g + g0, ibytes, &bar_full[slot]);
+                b2 += (size_t)GPS * 8;
+                if (kn > 0) {
+                    bulk_g2s(b2, A.kt_slot + kb, (unsigned)(kn * 4), &bar_full[slot]);
+                    bulk_g2s(b2 + (size_t)MK * 4, ktv + kb, (unsigned)(kn * sizeof(T)), &bar_full[slot]);
+                }
+            }
+            loadedc += nch;
+            d0 = n0;
+            d1 = n1;
+        }
+        if (q < npass) {
+            // gave up: let the copies already issued land before the CTA can exit
+            for (int qq = max(0, q - NB); qq < q; ++qq)
+                if (!mbar_wait(&bar_full[qq % NB], (qq / NB) & 1, A.err)) break;
+        }
+        return;
+    }
+    // ---- consumers (shared memory read through explicit 32-bit shared addresses)
+    const T* rom = reinterpret_cast<const T*>(A.romega) + (size_t)s * n;
+    const bool wcol = t0 + CW > P - 1;   // this CTA holds the w_1 column
+    const unsigned sX = smem_addr(rX) + EL * lane * (unsigned)sizeof(T);
+    const unsigned sV = smem_addr(rV) + EL * lane * (unsigned)sizeof(T);
+    const unsigned sB = smem_addr(bufs);
+    const unsigned oRR = (unsigned)(ME * RB), oGI = oRR + GPS * R * 16, oKS = oGI + GPS * 8, oKV = oKS + MK * 4;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int slot = pass % NB;
+        if (!mbar_wait(&bar_full[slot], (pass / NB) & 1, A.err)) break;
+        const int g = pass * GPS + warp;
+        if (g < ng) {
+            const unsigned buf = sB + (unsigned)(slot * bufsz);
+            const int2 gi = lds_i2(buf + oGI + warp * 8);
+            int4 rr[R];
+            T romv[R];
 #pragma unroll
-        for (int h = 0; h < G / 8; ++h) {
-            const int i = g0 + warp + 8 * h;
-            if (i < n) {
-                T acc0 = T(0), acc1 = T(0);
-                // the row's entries are fetched by the lanes in one round trip, then broadcast
-                const int e0 = A.cs_ptr[i], e1 = A.cs_ptr[i + 1];
-                for (int eb = e0; eb < e1; eb += 32) {
-                    const int e = eb + lane, cnt = min(32, e1 - eb);
-                    int sl_l = 0;
-                    T a_l = T(0), b_l = T(0);
-                    if (e < e1) {
-                        sl_l = A.cs_slot[e];
-                        a_l = Aop[e];
-                        b_l = Bop[e];
+            for (int r = 0; r < R; ++r) {
+                const uint4 u = lds_u4(buf + oRR + (warp * R + r) * 16);
+                rr[r] = make_int4((int)u.x, (int)u.y, (int)u.z, (int)u.w);
+                romv[r] = (wcol && rr[r].x >= 0) ? rom[rr[r].x] : T(0);
+            }
+            const unsigned mb = buf + gi.x * RB;
+            T acc[R][EL];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < EL; ++c) acc[r][c] = T(0);
+#pragma unroll 2
+            for (int e = 0; e < gi.y; ++e) {
+                unsigned wd[RW4];
+#pragma unroll
+                for (int k = 0; k < RB / 16; ++k) {
+                    const uint4 u = lds_u4(mb + e * RB + 16 * k);
+                    wd[4 * k] = u.x;
+                    wd[4 * k + 1] = u.y;
+                    wd[4 * k + 2] = u.z;
+                    wd[4 * k + 3] = u.w;
+                }
+                const unsigned off = wd[0] * (unsigned)(CW * sizeof(T));
+                T x[EL], v[EL];
+                if constexpr (EL == 2) {
+                    const float2 xx = lds_f2(sX + off);
+                    const float2 vv = lds_f2(sV + off);
+                    x[0] = xx.x;
+                    x[1] = xx.y;
+                    v[0] = vv.x;
+                    v[1] = vv.y;
+                } else {
+                    x[0] = lds_t<T>(sX + off);
+                    v[0] = lds_t<T>(sV + off);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    T a, bb;
+                    if constexpr (sizeof(T) == 4) {
+                        a = __uint_as_float(wd[2 + r]);
+                        bb = __uint_as_float(wd[2 + R + r]);
+                    } else {
+                        a = __hiloint2double((int)wd[2 + 2 * r + 1], (int)wd[2 + 2 * r]);
+                        bb = __hiloint2double((int)wd[2 + 2 * (R + r) + 1], (int)wd[2 + 2 * (R + r)]);
                     }
-                    for (int q = 0; q < cnt; ++q) {
-                        const int sl = __shfl_sync(0xffffffffu, sl_l, q);
-                        const T av = __shfl_sync(0xffffffffu, a_l, q);
-                        const T bv = __shfl_sync(0xffffffffu, b_l, q);
-                        const T2 x = *reinterpret_cast<const T2*>(rX + sl * 64 + 2 * lane);
-                        const T2 v = *reinterpret_cast<const T2*>(rV + sl * 64 + 2 * lane);
-                        acc0 += av * x.x + bv * v.x;
-                        acc1 += av * x.y + bv * v.y;
+#pragma unroll
+                    for (int c = 0; c < EL; ++c) acc[r][c] += a * x[c] + bb * v[c];
+                }
+            }
+            // - K_t(q_k) X, then the store
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = rr[r].x;
+                if (i < 0) continue;
+                for (int e = rr[r].y; e < rr[r].z; ++e) {
+                    const unsigned off = (unsigned)lds_i(buf + oKS + 4 * e) * (unsigned)(CW * sizeof(T));
+                    const T kv = lds_t<T>(buf + oKV + e * (unsigned)sizeof(T));
+                    if constexpr (EL == 2) {
+                        const float2 xx = lds_f2(sX + off);
+                        acc[r][0] -= kv * xx.x;
+                        acc[r][1] -= kv * xx.y;
+                    } else {
+                        acc[r][0] -= kv * lds_t<T>(sX + off);
                     }
                 }
-                const int k0 = A.kt_ptr[i], k1 = A.kt_ptr[i + 1];
-                for (int eb = k0; eb < k1; eb += 32) {
-                    const int e = eb + lane, cnt = min(32, k1 - eb);
-                    int sl_l = 0;
-                    T k_l = T(0);
-                    if (e < k1) {
-                        sl_l = A.kt_slot[e];
-                        k_l = ktv[e];
-                    }
-                    for (int q = 0; q < cnt; ++q) {
-                        const int sl = __shfl_sync(0xffffffffu, sl_l, q);
-                        const T kv = __shfl_sync(0xffffffffu, k_l, q);
-                        const T2 x = *reinterpret_cast<const T2*>(rX + sl * 64 + 2 * lane);
-                        acc0 -= kv * x.x;
-                        acc1 -= kv * x.y;
-                    }
+                const int t = t0 + EL * lane;
+#pragma unroll
+                for (int c = 0; c < EL; ++c)
+                    if (t + c == P - 1) acc[r][c] += romv[r];
+                if (t < ld) {
+                    if constexpr (EL == 2)
+                        *reinterpret_cast<float2*>(Y + (size_t)i * ld + t) = make_float2(acc[r][0], acc[r][1]);
+                    else
+                        Y[(size_t)i * ld + t] = acc[r][0];
                 }
-                const int t = t0 + 2 * lane;
-                if (t == P - 1) acc0 += rom[i];
-                if (t + 1 == P - 1) acc1 += rom[i];
-                if (t < ld) *reinterpret_cast<T2*>(Y + (size_t)i * ld + t) = T2{acc0, acc1};
             }
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_empty[slot]);
     }
-    cp_async_wait0();
+}
+
+// group records for the current w_1: slot, then A (R values), B (R values); fill entries 0
+template <typename T>
+__global__ void k_build_groups(int nE, int R, int RB, const int* __restrict__ map, const int* __restrict__ slot,
+                               const T* __restrict__ Aop, const T* __restrict__ Bop, unsigned char* rec) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+        unsigned char* m = rec + (size_t)e * RB;
+        *reinterpret_cast<int*>(m) = slot[e];
+        *reinterpret_cast<int*>(m + 4) = 0;
+        T* val = reinterpret_cast<T*>(m + 8);
+        for (int r = 0; r < R; ++r) {
+            const int q = map[(size_t)e * R + r];
+            val[r] = q >= 0 ? Aop[q] : T(0);
+            val[R + r] = q >= 0 ? Bop[q] : T(0);
+        }
+        for (size_t o = 8 + 2 * R * sizeof(T); o < (size_t)RB; o += 4) *reinterpret_cast<int*>(m + o) = 0;
+    }
 }
 
 // The per-block factor tiles of the blocked solves: Lt[c][r] (b x 32) and the 32 x 32
@@ -369,7 +583,70 @@ __global__ void k_sens_init(int N, int n, int ld, T* X, T* V) {
 
 size_t rhs_smem(const Params& p) {
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
-    return (size_t)2 * p.RW * 64 * tsz;
+    const size_t cw = tsz == 4 ? 64 : 32;
+    const size_t buf = (size_t)p.ME * p.RB + (size_t)FSE_RHS_GPS * p.R * 16 + (size_t)FSE_RHS_GPS * 8 +
+                       (size_t)p.MK * (4 + tsz);
+    const int dep = tsz == 4 ? FSE_RHS_DEPTH_F32 : FSE_RHS_DEPTH_F64;
+    return 128 + (size_t)2 * p.RW * cw * tsz + (size_t)(dep + 1) * buf;
+}
+
+int make_tangent_maps(fse_ctx* c) {
+    using encode_fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static encode_fn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return FSE_ECUDA;
+        encode = reinterpret_cast<encode_fn>(fn);
+    }
+    const Params& p = c->p;
+    const bool f32 = p.prec == FSE_MIXED_FP32;
+    const size_t tsz = f32 ? 4 : 8;
+    const cuuint32_t cw = f32 ? 64 : 32;
+    const cuuint64_t dims[3] = {(cuuint64_t)p.ld, (cuuint64_t)p.n, (cuuint64_t)p.N};
+    const cuuint64_t strides[2] = {(cuuint64_t)p.ld * tsz, (cuuint64_t)p.n * p.ld * tsz};
+    const cuuint32_t box[3] = {cw, 32, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    for (int k = 0; k < 2; ++k) {
+        CUtensorMap* m = k ? &c->tmV : &c->tmX;
+        void* ptr = k ? c->d.V : c->d.X;
+        if (encode(m, dt, 3, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return FSE_ECUDA;
+    }
+    return FSE_OK;
+}
+
+void launch_build_groups(fse_ctx* c) {
+    const Params& p = c->p;
+    const int g = nblocks(p.nE, 256);
+    if (p.prec == FSE_MIXED_FP32)
+        k_build_groups<float><<<g, 256, 0, c->stream>>>(p.nE, p.R, p.RB, c->d.g_map, c->d.g_slot,
+                                                        (const float*)c->d.cs_A, (const float*)c->d.cs_B,
+                                                        (unsigned char*)c->d.g_rec);
+    else
+        k_build_groups<double><<<g, 256, 0, c->stream>>>(p.nE, p.R, p.RB, c->d.g_map, c->d.g_slot,
+                                                         (const double*)c->d.cs_A, (const double*)c->d.cs_B,
+                                                         (unsigned char*)c->d.g_rec);
+}
+
+template <typename T, int R>
+static void rhs_launch(fse_ctx* c, const SensArgs& A, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sens_rhs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr = true;
+    }
+    const Params& p = c->p;
+    constexpr int CW = sizeof(T) == 4 ? 64 : 32;
+    dim3 g((p.P + CW - 1) / CW, p.N);
+    k_sens_rhs<T, R><<<g, 32 * (FSE_RHS_GPS + 1), p.smem_rhs, st>>>(A, c->tmX, c->tmV);
 }
 
 size_t trsm_smem(const Params& p) {
@@ -382,7 +659,6 @@ static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t s
     const Params& p = c->p;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_sens_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, true, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, true, 28>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -390,8 +666,12 @@ static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t s
         attr = true;
     }
     if (phase == 0) {
-        dim3 g((p.P + 63) / 64, p.N);
-        k_sens_rhs<T><<<g, 256, p.smem_rhs, st>>>(A);
+        switch (p.R) {
+            case 1: rhs_launch<T, 1>(c, A, st); break;
+            case 2: rhs_launch<T, 2>(c, A, st); break;
+            case 3: rhs_launch<T, 3>(c, A, st); break;
+            default: rhs_launch<T, 4>(c, A, st); break;
+        }
     } else {
         dim3 g((p.P + 127) / 128, p.N);
         const bool small = p.b <= 96;   // factor tile of b x 32 spread over 256 threads
@@ -429,18 +709,22 @@ void launch_sens_phase(fse_ctx* c, int k, double w, int phase, cudaStream_t st) 
     A.b = p.b;
     A.P = p.P;
     A.ld = p.ld;
-    A.nnz_kt = p.nnz_kt;
+    A.kt_ld = p.kt_ld;
+    A.MK = p.MK;
     A.nblk = p.nblk;
     A.RW = p.RW;
     A.RWT = p.RWT;
     A.a2c = 2.0 / Dl;
-    A.cs_ptr = c->d.cs_ptr;
-    A.cs_slot = c->d.cs_slot;
-    A.kt_ptr = c->d.kt_ptr;
+    A.ng = p.ng;
+    A.ME = p.ME;
+    A.RB = p.RB;
+    A.g_rr = c->d.g_rr;
+    A.g_info = c->d.g_info;
+    A.g_pass = c->d.g_pass;
+    A.g_rec = c->d.g_rec;
     A.kt_slot = c->d.kt_slot;
-    A.Aop = c->d.cs_A;
-    A.Bop = c->d.cs_B;
-    const size_t ktsz = (size_t)p.N * p.nnz_kt * tsz;
+    A.err = c->d.flag;
+    const size_t ktsz = (size_t)p.N * p.kt_ld * tsz;
     const size_t fsz = (size_t)p.N * p.n * (p.b + 1) * tsz;
     const size_t vsz = (size_t)p.N * p.n * tsz;
     const size_t dsz = (size_t)p.N * p.nblk * FSE_BLK * FSE_BLK * tsz;

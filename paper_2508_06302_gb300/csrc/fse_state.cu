@@ -178,7 +178,7 @@ __device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int 
 // ----------------------------------------------------------------------------
 
 struct StateArgs {
-    int n, b, e, dm1, maxit, ncolors, n_el, nnz_kt, nblk, init;
+    int n, b, e, dm1, maxit, ncolors, n_el, nnz_kt, kt_ld, nblk, init;
     double tol, Dl, a0c, a1c, a2c, w, phi;
     double rho[FSE_MAX_D - 1];
     const double *F, *phis;
@@ -188,7 +188,7 @@ struct StateArgs {
     const double* el_p;
     const int *kt_ptr, *kt_col, *kt_soff, *kt_src;
     double* ke;
-    void* kt_out;       // N x nnz_kt, K_t at the new state
+    void* kt_out;       // N x kt_ld, K_t at the new state
     void* romega;       // N x n, w_1-column term of this step (regular steps)
     const double *LMc, *LMr, *LMinv;
     double *q, *u, *a;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     T* oLr = reinterpret_cast<T*>(A.oLr) + foff;
     T* oLi = reinterpret_cast<T*>(A.oLinv) + off;
     T* oDi = reinterpret_cast<T*>(A.oDinv) + doff;
-    T* kt_out = reinterpret_cast<T*>(A.kt_out) + (size_t)s * A.nnz_kt;
+    T* kt_out = reinterpret_cast<T*>(A.kt_out) + (size_t)s * A.kt_ld;
     fill_tri_table(b, tab);
     if (tid == 0) {
         s_stat = A.init ? 0 : A.status[s];
@@ -573,6 +573,7 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.ncolors = p.ncolors;
     A.n_el = p.n_el;
     A.nnz_kt = p.nnz_kt;
+    A.kt_ld = p.kt_ld;
     A.nblk = p.nblk;
     A.init = init;
     A.tol = p.tol;
@@ -600,7 +601,7 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.kt_soff = c->d.kt_soff;
     A.kt_src = c->d.kt_src;
     A.ke = c->d.ke;
-    const size_t ktsz = (size_t)p.N * p.nnz_kt * tsz;
+    const size_t ktsz = (size_t)p.N * p.kt_ld * tsz;
     const size_t fsz = (size_t)p.N * p.n * (p.b + 1) * tsz;
     const size_t vsz = (size_t)p.N * p.n * tsz;
     const size_t dsz = (size_t)p.N * p.nblk * FSE_BLK * FSE_BLK * tsz;
