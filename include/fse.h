@@ -153,10 +153,33 @@ int fse_jacobian_dense(fse_ctx* ctx, double* J);
 int fse_monodromy(fse_ctx* ctx, double* Phi, double* dz_dw);
 
 /* One Newton-Raphson update of Z(0) at fixed w_1 (Sec. 3.3 step 6): evaluates
- * R and J at Z0, solves J dZ = -R on the GPU (dense LU with partial pivoting,
- * for 2 n U~ <= 16384) and overwrites Z0 <- Z0 + dZ.  res_norm_out receives
- * ||R(Z0_in)||_2.  Returns the evaluation status. */
+ * R and J at Z0, solves J dZ = -R on the GPU with the solver chosen by
+ * fse_set_linear_solver (dense LU up to 16384 unknowns, matrix-free GMRES
+ * above by default) and overwrites Z0 <- Z0 + dZ.  res_norm_out receives
+ * ||R(Z0_in)||_2.  Returns the evaluation status, FSE_ENOCONV also when GMRES
+ * stops above its tolerance (the update is still applied). */
 int fse_newton_step(fse_ctx* ctx, double* Z0, double omega1, double* res_norm_out);
+
+/* Outer linear solver of fse_newton_step and fse_continue (Sec. 3.3 step 6,
+ * J dZ = -R with J of Eq. 22).  FSE_LIN_DENSE: the dense J is formed on the
+ * GPU and factorised by LU with partial pivoting (2 n U~ <= 16384);
+ * FSE_LIN_GMRES: restarted GMRES(restart) in FP64 on the structured products
+ * J v = (I (x) R Gamma^-1) blockdiag(Phi_s) (I (x) Gamma) v - v, which read the
+ * monodromies in place (no dense J), stopped at ||J dZ + R|| <= rel_tol ||R||
+ * or after max_iters products; FSE_LIN_AUTO (default): dense up to 16384
+ * unknowns, GMRES above.  Defaults rel_tol 1e-8, restart 40, max_iters 400.
+ * The GMRES basis ((restart + 1) x 2 n U~ doubles) is allocated on first use
+ * and kept by the context.  Returns FSE_EINVAL for an unknown kind or
+ * restart outside [1, 256]. */
+#define FSE_LIN_AUTO 0
+#define FSE_LIN_DENSE 1
+#define FSE_LIN_GMRES 2
+int fse_set_linear_solver(fse_ctx* ctx, int kind, double rel_tol, int restart, int max_iters);
+
+/* Statistics of the last outer linear solve: Krylov iterations (0 for the
+ * dense solve) and the relative residual ||J dZ + R|| / ||R|| it reached
+ * (GMRES estimate; 0 for the dense solve). */
+int fse_linear_stats(const fse_ctx* ctx, int* iters, double* rel_res);
 
 /* First-order Lyapunov exponents (App. F) of the torus at (Z0, w_1), 1/s,
  * from the monodromy by-product: Psi_s = diag(I, w_1 I) Phi_s diag(I, I/w_1)
@@ -275,8 +298,8 @@ int fse_pod_build(const double* snaps, int nu, int m, int r, double* mean, doubl
  * rebuilt every pod_every points from all accepted points and the network is
  * trained on their coefficients (each mode divided by its RMS over the
  * accepted points, the scale the prediction multiplies back) for train_steps
- * Adam steps after every point.  The outer linear solve is the dense LU of
- * fse_newton_step (problems up to 16384 unknowns).
+ * Adam steps after every point.  The outer linear solve is the one of
+ * fse_newton_step (fse_set_linear_solver).
  * ------------------------------------------------------------------------ */
 #define FSE_PRED_SECANT 0
 #define FSE_PRED_MLP 1
@@ -293,6 +316,9 @@ typedef struct {
     int train_steps;           /* Adam steps after each accepted point          */
     float lr;                  /* Adam learning rate                            */
     double omega_lo, omega_hi; /* normalisation range of w_1                    */
+    int chord;                 /* 1: corrector updates reuse the Jacobian of the
+                                  point's first evaluation (chord Newton; later
+                                  evaluations residual only); 0: full Newton  */
 } fse_cont_opts;
 
 typedef struct {

@@ -590,6 +590,40 @@ __global__ void k_pod_project(size_t nu, int r, const double* mean, const double
     if (threadIdx.x == 0) coef[(size_t)j * r + k] = red[0];
 }
 
+// out[i] = V_i . w, one block per Krylov vector
+__global__ void k_mdot(size_t n, const double* __restrict__ V, const double* __restrict__ w, double* out) {
+    const int i = blockIdx.x;
+    __shared__ double red[512];
+    double acc = 0.0;
+    const double* v = V + (size_t)i * n;
+    for (size_t x = threadIdx.x; x < n; x += blockDim.x) acc += v[x] * w[x];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = red[0];
+}
+
+// w += sum_{i<k} coef[i] V_i
+__global__ void k_mupdate(size_t n, int k, const double* __restrict__ V, const double* __restrict__ coef,
+                          double* w) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+        double acc = w[x];
+        for (int i = 0; i < k; ++i) acc += coef[i] * V[(size_t)i * n + x];
+        w[x] = acc;
+    }
+}
+
+void vec_mdot(fse_ctx* c, size_t n, int k, const double* V, const double* w, double* out_dev) {
+    k_mdot<<<k, 512, 0, c->stream>>>(n, V, w, out_dev);
+}
+
+void vec_mupdate(fse_ctx* c, size_t n, int k, const double* V, const double* coef_dev, double* w) {
+    k_mupdate<<<nblocks(n, 256), 256, 0, c->stream>>>(n, k, V, coef_dev, w);
+}
+
 void vec_axpby(fse_ctx* c, size_t n, double a, const double* x, double b, double* y) {
     k_axpby<<<nblocks(n, 256), 256, 0, c->stream>>>(n, a, x, b, y);
 }

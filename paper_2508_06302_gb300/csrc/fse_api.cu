@@ -120,7 +120,7 @@ static void free_ctx(fse_ctx* c) {
                     c->d.kt_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
                     c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
                     c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
-                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv};
+                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv, c->kry, c->kdot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -823,33 +823,197 @@ static int eval_at_iterate(fse_ctx* c, double w, int sens, double* rn, double* z
     return rc ? rc : st;
 }
 
+// w = J v with the stored monodromies (Eq. 22): i-DFT, blockdiag(Phi_s), DFT + rotation, minus v
+static void jac_apply_dev(fse_ctx* c, const double* v, double* w) {
+    fse::launch_idft(c, v, c->d.zb);
+    fse::launch_phi_apply(c, c->d.zb, c->d.yb);
+    fse::launch_dft_residual(c, c->d.yb, v, w, 1);
+}
+
+// Restarted GMRES(m) on J x = b (b, x on the device, x0 = 0), FP64, classical Gram-Schmidt with
+// one re-orthogonalisation pass; the small Hessenberg least-squares problem is reduced by
+// Givens rotations on the host.  Returns FSE_OK, or FSE_ENOCONV when it stops above rtol.
+static int gmres_dev(fse_ctx* c, const double* b, double* x, double rtol, int m, int maxit, int* iters_out,
+                     double* relres_out) {
+    const size_t n = (size_t)2 * c->p.n * c->p.U;
+    if ((size_t)(m + 1) * n > c->kry_cap) {
+        if (c->kry) cudaFree(c->kry);
+        if (c->kdot) cudaFree(c->kdot);
+        c->kry = nullptr;
+        c->kdot = nullptr;
+        c->kry_cap = 0;
+        cudaError_t e = cudaMalloc(&c->kry, (size_t)(m + 1) * n * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&c->kdot, (size_t)2 * (m + 2) * 8);
+        if (e != cudaSuccess) return cuda_check(c, e, "GMRES basis");
+        c->kry_cap = (size_t)(m + 1) * n;
+    }
+    double* Vb = c->kry;
+    double* hd = c->kdot;
+    auto norm2 = [&](const double* v, double* out) -> int {
+        fse::vec_norms2(c, n, v, nullptr, hd);
+        double h2[2];
+        cudaMemcpyAsync(h2, hd, 16, cudaMemcpyDeviceToHost, c->stream);
+        const int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "GMRES norm");
+        *out = std::sqrt(h2[0]);
+        return rc;
+    };
+    cudaMemsetAsync(x, 0, n * 8, c->stream);
+    double bn = 0.0;
+    int rc = norm2(b, &bn);
+    if (rc) return rc;
+    int it = 0;
+    double rel = 0.0;
+    if (!(bn > 0.0)) {
+        *iters_out = 0;
+        *relres_out = 0.0;
+        return FSE_OK;
+    }
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hcol(m + 2), h2(m + 2);
+    bool first = true;
+    while (it < maxit) {
+        // r = b - J x  (x = 0 on the first cycle)
+        double* v0 = Vb;
+        if (first) {
+            cudaMemcpyAsync(v0, b, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+        } else {
+            jac_apply_dev(c, x, v0);
+            fse::vec_axpby(c, n, 1.0, b, -1.0, v0);
+        }
+        first = false;
+        double beta = 0.0;
+        rc = norm2(v0, &beta);
+        if (rc) return rc;
+        rel = beta / bn;
+        if (rel <= rtol) break;
+        fse::vec_axpby(c, n, 0.0, v0, 1.0 / beta, v0);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        for (; k < m && it < maxit; ++k) {
+            double* w = Vb + (size_t)(k + 1) * n;
+            jac_apply_dev(c, Vb + (size_t)k * n, w);
+            ++it;
+            // two passes of classical Gram-Schmidt against v_0..v_k
+            std::fill(hcol.begin(), hcol.end(), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                fse::vec_mdot(c, n, k + 1, Vb, w, hd);
+                cudaMemcpyAsync(h2.data(), hd, (size_t)(k + 1) * 8, cudaMemcpyDeviceToHost, c->stream);
+                rc = cuda_check(c, cudaStreamSynchronize(c->stream), "GMRES dots");
+                if (rc) return rc;
+                for (int i = 0; i <= k; ++i) {
+                    hcol[i] += h2[i];
+                    h2[i] = -h2[i];
+                }
+                cudaMemcpyAsync(hd + (m + 2), h2.data(), (size_t)(k + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+                fse::vec_mupdate(c, n, k + 1, Vb, hd + (m + 2), w);
+            }
+            double hn = 0.0;
+            rc = norm2(w, &hn);
+            if (rc) return rc;
+            hcol[k + 1] = hn;
+            if (hn > 0.0) fse::vec_axpby(c, n, 0.0, w, 1.0 / hn, w);
+            // apply the previous rotations, then a new one that zeroes hcol[k + 1]
+            for (int i = 0; i < k; ++i) {
+                const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = t;
+            }
+            const double r = std::hypot(hcol[k], hcol[k + 1]);
+            cs[k] = r > 0.0 ? hcol[k] / r : 1.0;
+            sn[k] = r > 0.0 ? hcol[k + 1] / r : 0.0;
+            hcol[k] = r;
+            hcol[k + 1] = 0.0;
+            g[k + 1] = -sn[k] * g[k];
+            g[k] = cs[k] * g[k];
+            for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = hcol[i];
+            rel = std::fabs(g[k + 1]) / bn;
+            if (rel <= rtol || hn == 0.0) {
+                ++k;
+                break;
+            }
+        }
+        // x += V_k y with R y = g (upper triangular back substitution)
+        for (int i = k - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int j = i + 1; j < k; ++j) t -= H[(size_t)i * m + j] * y[j];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? t / H[(size_t)i * m + i] : 0.0;
+        }
+        cudaMemcpyAsync(hd + (m + 2), y.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream);
+        fse::vec_mupdate(c, n, k, Vb, hd + (m + 2), x);
+        rc = cuda_check(c, cudaStreamSynchronize(c->stream), "GMRES update");
+        if (rc) return rc;
+        if (rel <= rtol) break;
+    }
+    *iters_out = it;
+    *relres_out = rel;
+    return rel <= rtol ? FSE_OK : FSE_ENOCONV;
+}
+
 // Solve J dZ = -R (Jacobian and R of the last evaluation) and update d.Z0 += dZ, on the device.
+// Returns FSE_OK, FSE_ENOCONV (GMRES stopped above its tolerance; the update is applied) or an error.
 static int newton_solve_update(fse_ctx* c) {
     const size_t m = (size_t)2 * c->p.n * c->p.U;
-    if (m > 16384) return set_err(c, FSE_EINVAL, "outer solve: dense LU limited to 16384 unknowns");
-    int rc = ensure_dense(c, m);
-    if (rc) return rc;
-    fse::launch_dense_jac(c, c->Jd);
-    fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, c->d.vec);       // rhs = -R
-    rc = fse::dense_lu_solve(c, c->Jd, c->d.vec, (int)m);
-    if (rc) return set_err(c, rc, "singular shooting Jacobian");
-    fse::vec_axpby(c, m, 1.0, c->d.vec, 1.0, c->d.Z0);       // Z0 += dZ
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "newton update");
+    const bool dense = c->lin_kind == FSE_LIN_DENSE || (c->lin_kind == FSE_LIN_AUTO && m <= 16384);
+    c->lin_iters = 0;
+    c->lin_relres = 0.0;
+    if (dense) {
+        if (m > 16384) return set_err(c, FSE_EINVAL, "outer solve: dense LU limited to 16384 unknowns");
+        int rc = ensure_dense(c, m);
+        if (rc) return rc;
+        fse::launch_dense_jac(c, c->Jd);
+        fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, c->d.vec);       // rhs = -R
+        rc = fse::dense_lu_solve(c, c->Jd, c->d.vec, (int)m);
+        if (rc) return set_err(c, rc, "singular shooting Jacobian");
+        fse::vec_axpby(c, m, 1.0, c->d.vec, 1.0, c->d.Z0);       // Z0 += dZ
+        return cuda_check(c, cudaStreamSynchronize(c->stream), "newton update");
+    }
+    fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, c->d.vec2);          // rhs = -R
+    int it = 0;
+    double rel = 0.0;
+    const int rc = gmres_dev(c, c->d.vec2, c->d.vec, c->lin_rtol, c->lin_restart, c->lin_maxit, &it, &rel);
+    c->lin_iters = it;
+    c->lin_relres = rel;
+    if (rc != FSE_OK && rc != FSE_ENOCONV) return rc;
+    fse::vec_axpby(c, m, 1.0, c->d.vec, 1.0, c->d.Z0);           // Z0 += dZ
+    const int rc2 = cuda_check(c, cudaStreamSynchronize(c->stream), "newton update");
+    if (rc2) return rc2;
+    if (rc == FSE_ENOCONV) c->err = "GMRES stopped above its tolerance";
+    return rc;
+}
+
+extern "C" int fse_set_linear_solver(fse_ctx* c, int kind, double rel_tol, int restart, int max_iters) {
+    if (!c) return FSE_EINVAL;
+    if (kind != FSE_LIN_AUTO && kind != FSE_LIN_DENSE && kind != FSE_LIN_GMRES)
+        return set_err(c, FSE_EINVAL, "unknown linear solver");
+    if (restart < 1 || restart > 256 || max_iters < 1 || !(rel_tol > 0.0))
+        return set_err(c, FSE_EINVAL, "need rel_tol > 0, 1 <= restart <= 256, max_iters >= 1");
+    c->lin_kind = kind;
+    c->lin_rtol = rel_tol;
+    c->lin_restart = restart;
+    c->lin_maxit = max_iters;
+    return FSE_OK;
+}
+
+extern "C" int fse_linear_stats(const fse_ctx* c, int* iters, double* rel_res) {
+    if (!c) return FSE_EINVAL;
+    if (iters) *iters = c->lin_iters;
+    if (rel_res) *rel_res = c->lin_relres;
+    return FSE_OK;
 }
 
 extern "C" int fse_newton_step(fse_ctx* c, double* Z0, double w, double* res_norm) {
     if (!c || !Z0) return FSE_EINVAL;
     const size_t m = (size_t)2 * c->p.n * c->p.U;
-    if (m > 16384) return set_err(c, FSE_EINVAL, "fse_newton_step: dense solve limited to 16384 unknowns");
     cudaSetDevice(c->device);
     cudaMemcpyAsync(c->d.Z0, Z0, m * 8, cudaMemcpyHostToDevice, c->stream);
     const int st = eval_at_iterate(c, w, 1, res_norm, nullptr);
     if (st < 0 && st != FSE_ENOCONV) return st;
-    int rc = newton_solve_update(c);
-    if (rc) return rc;
+    const int lin = newton_solve_update(c);
+    if (lin != FSE_OK && lin != FSE_ENOCONV) return lin;
     cudaMemcpyAsync(Z0, c->d.Z0, m * 8, cudaMemcpyDeviceToHost, c->stream);
-    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step");
-    return rc ? rc : st;
+    const int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step");
+    if (rc) return rc;
+    return st != FSE_OK ? st : lin;
 }
 
 extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, int h, double* sigma) {
@@ -1007,7 +1171,7 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
         }
         while (st >= FSE_ENOCONV && rn > o->rel_tol * zn && it < o->max_newton) {
             int rc = newton_solve_update(c);
-            if (rc) {
+            if (rc && rc != FSE_ENOCONV) {
                 st = rc;
                 break;
             }
@@ -1015,6 +1179,7 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
             st = eval_at_iterate(c, w, 0, &rn, &zn);
             ++evals;
             if (rn <= o->rel_tol * zn || st < FSE_ENOCONV) break;
+            if (o->chord) continue;   // next update with the monodromies of the point's first evaluation
             st = eval_at_iterate(c, w, 1, &rn, &zn);
             ++evals;
         }

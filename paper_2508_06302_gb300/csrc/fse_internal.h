@@ -151,6 +151,16 @@ struct fse_ctx {
     double* Jd = nullptr;
     int* piv = nullptr;
     size_t Jd_cap = 0;
+    // outer linear solver: FSE_LIN_AUTO / FSE_LIN_DENSE / FSE_LIN_GMRES, GMRES(m) settings,
+    // its Krylov basis ((m + 1) x 2nU, allocated on first use) and the last solve's statistics
+    int lin_kind = FSE_LIN_AUTO;
+    double lin_rtol = 1e-8;
+    int lin_restart = 40, lin_maxit = 400;
+    double* kry = nullptr;
+    double* kdot = nullptr;       // device scratch for the Gram-Schmidt coefficients
+    size_t kry_cap = 0;
+    int lin_iters = 0;
+    double lin_relres = 0.0;
 };
 
 namespace fse {
@@ -188,6 +198,10 @@ int lyapunov_run_noalloc(fse_ctx* c, double omega1, int N_Ly, int h, double* sig
 // vector helpers on the context stream (fse_aft.cu)
 void vec_axpby(fse_ctx* c, size_t n, double a, const double* x, double b, double* y);
 void vec_norms2(fse_ctx* c, size_t n, const double* x, const double* y, double* out_dev);
+// out[i] = V_i . w for i < k (V: k x n row-major), one block per vector
+void vec_mdot(fse_ctx* c, size_t n, int k, const double* V, const double* w, double* out_dev);
+// w += sum_{i<k} coef[i] V_i  (coef on the device)
+void vec_mupdate(fse_ctx* c, size_t n, int k, const double* V, const double* coef_dev, double* w);
 void pod_expand(fse_ctx* c, size_t nu, int r, const double* mean, const double* basis, const double* coef,
                 double* z);
 void pod_project(fse_ctx* c, size_t nu, int r, int m, const double* mean, const double* basis, const double* Z,

@@ -26,6 +26,9 @@ FSE_ECUDA = -6
 FSE_ENOJAC = -7
 FSE_FP64 = 0
 FSE_MIXED_FP32 = 1
+FSE_LIN_AUTO = 0
+FSE_LIN_DENSE = 1
+FSE_LIN_GMRES = 2
 
 _PREC = {"fp64": FSE_FP64, "mixed_fp32": FSE_MIXED_FP32, "fp32": FSE_MIXED_FP32}
 
@@ -89,6 +92,8 @@ def load(path: Optional[str] = None):
         "fse_newton_step": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP]),
         "fse_lyapunov": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
         "fse_lyapunov_noalloc": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
+        "fse_set_linear_solver": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+        "fse_linear_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "fse_timings": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
         "fse_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
         "fse_set_steps": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -272,6 +277,18 @@ class Context:
         self._check(rc, (FSE_ENOCONV,))
         return Z, rn.value, rc
 
+    def set_linear_solver(self, kind="auto", rel_tol=1e-8, restart=40, max_iters=400):
+        """fse_set_linear_solver: kind in {"auto", "dense", "gmres"}."""
+        k = {"auto": FSE_LIN_AUTO, "dense": FSE_LIN_DENSE, "gmres": FSE_LIN_GMRES}[kind]
+        self._check(load().fse_set_linear_solver(self.h, k, float(rel_tol), int(restart), int(max_iters)))
+
+    def linear_stats(self):
+        """fse_linear_stats: (Krylov iterations, relative residual) of the last outer solve."""
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        self._check(load().fse_linear_stats(self.h, ctypes.byref(it), ctypes.byref(rr)))
+        return it.value, rr.value
+
     def lyapunov(self, Z0, omega1, N_Ly, h):
         Z = np.ascontiguousarray(Z0, dtype=np.float64)
         out = np.zeros(h)
@@ -388,7 +405,8 @@ class fse_cont_opts(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int), ("omega1", _DP), ("predictor", ctypes.c_int),
                 ("rel_tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("warmup", ctypes.c_int),
                 ("pod_modes", ctypes.c_int), ("pod_every", ctypes.c_int), ("train_steps", ctypes.c_int),
-                ("lr", ctypes.c_float), ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double)]
+                ("lr", ctypes.c_float), ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double),
+                ("chord", ctypes.c_int)]
 
 
 class fse_cont_point(ctypes.Structure):
@@ -398,7 +416,8 @@ class fse_cont_point(ctypes.Structure):
 
 
 def fse_continue(ctx, omegas, Z_start, predictor="secant", mlp=None, rel_tol=1e-10, max_newton=10,
-                 warmup=8, pod_modes=64, pod_every=8, train_steps=200, lr=1e-3, omega_range=None):
+                 warmup=8, pod_modes=64, pod_every=8, train_steps=200, lr=1e-3, omega_range=None,
+                 chord=False):
     """fse_continue(): returns (Z (n_points x nu), list of per-point dicts, rc)."""
     lib = load()
     if not hasattr(lib, "_cont_sig"):
@@ -412,7 +431,7 @@ def fse_continue(ctx, omegas, Z_start, predictor="secant", mlp=None, rel_tol=1e-
     P = om.size
     lo, hi = (float(om.min()), float(om.max())) if omega_range is None else omega_range
     o = fse_cont_opts(P, _dp(om), FSE_PRED_MLP if predictor == "mlp" else FSE_PRED_SECANT, rel_tol, max_newton,
-                      warmup, pod_modes, pod_every, train_steps, lr, lo, hi)
+                      warmup, pod_modes, pod_every, train_steps, lr, lo, hi, int(bool(chord)))
     Z0 = np.ascontiguousarray(Z_start, dtype=np.float64)
     Zout = np.zeros((P, Z0.size))
     info = (fse_cont_point * P)()
