@@ -3,6 +3,7 @@
 // stiffness in the sensitivity precision T.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -86,8 +87,12 @@ __device__ void fill_tri_table(int b, unsigned* tab) {
     }
 }
 
+// columns of the band staged ahead of the Cholesky window (cp.async ring)
+#define FSE_CHOL_PF 8
+
 template <typename T>
-__device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab) {
+__device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab, T* stg) {
+    constexpr int PF = FSE_CHOL_PF;
     const int nb = b + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ntri = b * (b + 1) / 2;
@@ -97,11 +102,17 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
         const int c = idx / nb;
         wnd[idx] = (c < n) ? Ac[(size_t)c * nb + (idx - c * nb)] : T(0);
     }
-    // the column entering the window at step j (column j + nb) is fetched one step ahead
-    T pref = (tid < nb && nb < n) ? Ac[(size_t)nb * nb + tid] : T(0);
+    // the column entering the window at step j (column j + nb) is staged PF - 1 steps ahead;
+    // thread r copies and later reads entry r of every staged column
+    auto issue = [&](int col) {
+        if (col < n && tid < nb) cp_async_elem(stg + (col % PF) * nb + tid, Ac + (size_t)col * nb + tid);
+        cp_async_commit();
+    };
+    for (int c = 0; c < PF - 1; ++c) issue(nb + c);
     __syncthreads();
     int slot = 0;   // window slot of column j (= j mod nb)
     for (int j = 0; j < n; ++j, slot = (slot + 1 == nb) ? 0 : slot + 1) {
+        issue(j + nb + PF - 1);
         T* colj = wnd + slot * nb;
         const T piv = colj[0];
         if (!(piv > T(0)) || !isfinite((double)piv)) {
@@ -123,9 +134,10 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
                 wnd[sc * nb + rr] -= colj[cc + rr] * colj[cc] * inv2;
             }
         }
+        cp_async_wait<PF - 1>();   // this thread's entry of column j + nb has landed
         __syncthreads();
-        // write column j of L out and load column j + nb into its slot (each thread owns
-        // the same entries r in both parts, so no barrier is needed between them)
+        // write column j of L out and move column j + nb into its slot (each thread owns
+        // the same entry r in all parts, so no barrier is needed between them)
         const int jn = j + nb;
         if (tid < nb) {   // nb <= blockDim.x: one entry per thread
             const int r = tid;
@@ -136,42 +148,46 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
                 Linv[j] = inv;
                 for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
             }
-            colj[r] = (jn < n) ? pref : T(0);
-            pref = (jn + 1 < n) ? Ac[(size_t)(jn + 1) * nb + r] : T(0);
+            colj[r] = (jn < n) ? stg[(jn % PF) * nb + r] : T(0);
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
     __syncthreads();
     return bad;
 }
 
-// inverses of the 32 x 32 diagonal blocks of L (one warp per block, one lane per column)
+// inverses of the 32 x 32 diagonal blocks of L (one warp per block, one lane per column);
+// the block's lower triangle is first copied to the warp's shared tile
 template <typename T>
-__device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int nblk, T* Dinv) {
+__device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int nblk, T* Dinv, T* tiles) {
     const int nb = b + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    T* Lt = tiles + (size_t)warp * (FSE_BLK * FSE_BLK + FSE_BLK);   // [i][j] j < i, then 1/L_ii
     for (int B = warp; B < nblk; B += nw) {
         const int i0 = B * FSE_BLK;
+        __syncwarp();
+        for (int idx = lane; idx < FSE_BLK * FSE_BLK; idx += 32) {
+            const int i = idx >> 5, j = idx & 31, gi = i0 + i, c = j - i + b;   // row band of L(gi, i0 + j)
+            Lt[idx] = (gi < n && j < i && c >= 0) ? Lr[(size_t)gi * nb + c] : T(0);
+        }
+        Lt[FSE_BLK * FSE_BLK + lane] = (i0 + lane < n) ? Linv[i0 + lane] : T(1);   // identity past n
+        __syncwarp();
         T z[FSE_BLK];
 #pragma unroll
         for (int i = 0; i < FSE_BLK; ++i) {
-            const int gi = i0 + i;
             T acc = (i == lane) ? T(1) : T(0);
-            if (gi < n) {
 #pragma unroll
-                for (int j = 0; j < i; ++j) {
-                    const int c = (i0 + j) - gi + b;   // row-band index of L(gi, i0 + j)
-                    if (c >= 0) acc -= Lr[(size_t)gi * nb + c] * z[j];
-                }
-                acc *= Linv[gi];
-            }
-            z[i] = acc;
+            for (int j = 0; j < i; ++j) acc -= Lt[i * FSE_BLK + j] * z[j];
+            z[i] = acc * Lt[FSE_BLK * FSE_BLK + i];
         }
         T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK;
 #pragma unroll
         for (int i = 0; i < FSE_BLK; ++i) D[i * FSE_BLK + lane] = z[i];
     }
+    __syncwarp();
 }
+
 
 // ----------------------------------------------------------------------------
 // the state kernel
@@ -257,69 +273,137 @@ __device__ void assemble_keff(const StateArgs& A, int s, const double* q, T* Ac,
     __syncthreads();
 }
 
-// Blocked banded solve L L^T x = r in place (r in shared memory, FP64 arithmetic,
-// factor of type T): 32-row blocks, off-diagonal band part as dot products,
-// diagonal blocks through their stored inverses.
+// Blocked banded solve L L^T x = r in place (r in shared memory, FP64 in and out) with the
+// arithmetic in the factor precision T: r is rounded to T once, both substitutions run in T
+// and x is widened back.  With the FP64 residual of the Newton iteration around it this is
+// iterative refinement, so the converged state keeps FP64 accuracy.  32-row blocks; the
+// off-diagonal band part as dot products (32 rows x 8 lanes); diagonal blocks through their
+// stored inverses.  For b <= 96 the next block's band entries and inverse are loaded into
+// registers while the current block computes.
 template <typename T>
 __device__ void cta_blocked_solve(const T* __restrict__ Lc, const T* __restrict__ Lr,
-                                  const T* __restrict__ Dinv, int n, int b, int nblk, double* r,
-                                  double* tmp) {
+                                  const T* __restrict__ Dinv, int n, int b, int nblk, double* r, T* y,
+                                  T* tmp) {
+    constexpr int MC = 12;                                     // band entries per lane (b <= 96)
     const int nb = b + 1;
     const int row = threadIdx.x >> 3, l8 = threadIdx.x & 7;   // 32 rows x 8 lanes
-    // forward: y_B = Dinv_B (r_B - L_{B,<} y_<)
+    const bool pf = b <= 8 * MC;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = T(r[i]);
+    __syncthreads();
+    T lcur[MC], lnxt[MC], dcur[4], dnxt[4];
+    // forward: y_B = Dinv_B (r_B - L_{B,<} y_<); lane l8 holds L(i, i0 - b + l8 + 8q)
+    auto fwd_load = [&](int B, T* lv, T* dv) {
+        const int i0 = B * FSE_BLK, i = i0 + row;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int c = l8 + 8 * q, j = i0 - b + c, bi = c - row;
+            lv[q] = (i < n && c < b && j >= 0 && bi >= 0) ? Lr[(size_t)i * nb + bi] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = l8 + 8 * q;
+            dv[q] = (k <= row) ? Dinv[(size_t)B * FSE_BLK * FSE_BLK + row * FSE_BLK + k] : T(0);
+        }
+    };
+    if (pf) fwd_load(0, lnxt, dnxt);
     for (int B = 0; B < nblk; ++B) {
         const int i0 = B * FSE_BLK, i = i0 + row;
-        double part = 0.0;
-        if (i < n && row < FSE_BLK) {
+        T part = T(0);
+        if (pf) {
+#pragma unroll
+            for (int q = 0; q < MC; ++q) lcur[q] = lnxt[q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dcur[q] = dnxt[q];
+            if (B + 1 < nblk) fwd_load(B + 1, lnxt, dnxt);
+#pragma unroll
+            for (int q = 0; q < MC; ++q) {
+                const int c = l8 + 8 * q, j = i0 - b + c;   // j < i0 <= n - 1 for c < b
+                if (c < b && j >= 0) part += lcur[q] * y[j];
+            }
+        } else if (i < n) {
             for (int c = l8; c < b; c += 8) {
-                const int j = i0 - b + c;        // column left of the block
-                const int bi = c - row;          // row-band index of L(i, j)
-                if (j >= 0 && bi >= 0) part += (double)Lr[(size_t)i * nb + bi] * r[j];
+                const int j = i0 - b + c, bi = c - row;
+                if (j >= 0 && bi >= 0) part += Lr[(size_t)i * nb + bi] * y[j];
             }
         }
         part += __shfl_xor_sync(0xffffffffu, part, 4);
         part += __shfl_xor_sync(0xffffffffu, part, 2);
         part += __shfl_xor_sync(0xffffffffu, part, 1);
-        if (l8 == 0 && row < FSE_BLK) tmp[row] = (i < n) ? r[i] - part : 0.0;
+        if (l8 == 0) tmp[row] = (i < n) ? y[i] - part : T(0);
         __syncthreads();
-        double y = 0.0;
-        if (row < FSE_BLK) {
+        T yv = T(0);
+        if (pf) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yv += dcur[q] * tmp[l8 + 8 * q];
+        } else {
             const T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK + row * FSE_BLK;
-            for (int k = l8; k <= row; k += 8) y += (double)D[k] * tmp[k];
+            for (int k = l8; k <= row; k += 8) yv += D[k] * tmp[k];
         }
-        y += __shfl_xor_sync(0xffffffffu, y, 4);
-        y += __shfl_xor_sync(0xffffffffu, y, 2);
-        y += __shfl_xor_sync(0xffffffffu, y, 1);
-        if (l8 == 0 && row < FSE_BLK && i < n) r[i] = y;
+        yv += __shfl_xor_sync(0xffffffffu, yv, 4);
+        yv += __shfl_xor_sync(0xffffffffu, yv, 2);
+        yv += __shfl_xor_sync(0xffffffffu, yv, 1);
+        if (l8 == 0 && i < n) y[i] = yv;
         __syncthreads();
     }
-    // backward: x_B = Dinv_B^T (y_B - L_{>,B}^T x_>)
+    // backward: x_B = Dinv_B^T (y_B - L_{>,B}^T x_>); lane l8 holds L(i0 + 32 + l8 + 8q, i)
+    auto bwd_load = [&](int B, T* lv, T* dv) {
+        const int i0 = B * FSE_BLK, i = i0 + row;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int c = l8 + 8 * q, k = i0 + FSE_BLK + c, ci = k - i;
+            lv[q] = (i < n && c < b && k < n && ci <= b) ? Lc[(size_t)i * nb + ci] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = row + l8 + 8 * q;
+            dv[q] = (k < FSE_BLK) ? Dinv[(size_t)B * FSE_BLK * FSE_BLK + k * FSE_BLK + row] : T(0);
+        }
+    };
+    if (pf) bwd_load(nblk - 1, lnxt, dnxt);
     for (int B = nblk - 1; B >= 0; --B) {
         const int i0 = B * FSE_BLK, i = i0 + row;
-        double part = 0.0;
-        if (i < n && row < FSE_BLK) {
+        T part = T(0);
+        if (pf) {
+#pragma unroll
+            for (int q = 0; q < MC; ++q) lcur[q] = lnxt[q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dcur[q] = dnxt[q];
+            if (B > 0) bwd_load(B - 1, lnxt, dnxt);
+#pragma unroll
+            for (int q = 0; q < MC; ++q) {
+                const int c = l8 + 8 * q, k = i0 + FSE_BLK + c;
+                if (c < b && k < n) part += lcur[q] * y[k];
+            }
+        } else if (i < n) {
             for (int c = l8; c < b; c += 8) {
-                const int k = i0 + FSE_BLK + c;  // row below the block
-                const int ci = k - i;            // column-band index of L(k, i)
-                if (k < n && ci <= b) part += (double)Lc[(size_t)i * nb + ci] * r[k];
+                const int k = i0 + FSE_BLK + c, ci = k - i;
+                if (k < n && ci <= b) part += Lc[(size_t)i * nb + ci] * y[k];
             }
         }
         part += __shfl_xor_sync(0xffffffffu, part, 4);
         part += __shfl_xor_sync(0xffffffffu, part, 2);
         part += __shfl_xor_sync(0xffffffffu, part, 1);
-        if (l8 == 0 && row < FSE_BLK) tmp[row] = (i < n) ? r[i] - part : 0.0;
+        if (l8 == 0) tmp[row] = (i < n) ? y[i] - part : T(0);
         __syncthreads();
-        double x = 0.0;
-        if (row < FSE_BLK) {
+        T xv = T(0);
+        if (pf) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = row + l8 + 8 * q;
+                if (k < FSE_BLK) xv += dcur[q] * tmp[k];
+            }
+        } else {
             const T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK;
-            for (int k = row + l8; k < FSE_BLK; k += 8) x += (double)D[k * FSE_BLK + row] * tmp[k];
+            for (int k = row + l8; k < FSE_BLK; k += 8) xv += D[k * FSE_BLK + row] * tmp[k];
         }
-        x += __shfl_xor_sync(0xffffffffu, x, 4);
-        x += __shfl_xor_sync(0xffffffffu, x, 2);
-        x += __shfl_xor_sync(0xffffffffu, x, 1);
-        if (l8 == 0 && row < FSE_BLK && i < n) r[i] = x;
+        xv += __shfl_xor_sync(0xffffffffu, xv, 4);
+        xv += __shfl_xor_sync(0xffffffffu, xv, 2);
+        xv += __shfl_xor_sync(0xffffffffu, xv, 1);
+        if (l8 == 0 && i < n) y[i] = xv;
         __syncthreads();
     }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = (double)y[i];
+    __syncthreads();
 }
 
 // Single-warp banded solve of the FP64 mass factor (setup-time layouts), used once per
@@ -356,10 +440,15 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     const int tid = threadIdx.x, nt = blockDim.x;
     extern __shared__ double sm[];
     double *sq = sm, *su = sq + n, *sa = su + n, *sqn = sa + n, *sb = sqn + n, *sr = sb + n;
-    double* tmp = sr + n;                                 // 32
-    unsigned* tab = reinterpret_cast<unsigned*>(tmp + FSE_BLK);
+    T* tmp = reinterpret_cast<T*>(sr + n);                // 32
+    unsigned* tab = reinterpret_cast<unsigned*>(sr + n + FSE_BLK);
     const int ntri = b * (b + 1) / 2;
+    // Cholesky window (nb x nb) and staging ring (FSE_CHOL_PF x nb); the diagonal-block tiles
+    // of cta_diag_inverses reuse the same space once the factorisation is done
     T* wnd = reinterpret_cast<T*>(tab + ((ntri + 1) & ~1));
+    T* stg = wnd + (size_t)nb * nb;
+    const size_t wspan = max((size_t)nb * nb + (size_t)FSE_CHOL_PF * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
+    T* ysol = wnd + wspan;                                // n: solve vector in the factor precision
     __shared__ int s_conv, s_stat;
     const size_t off = (size_t)s * n;
     const size_t foff = (size_t)s * n * nb;
@@ -422,7 +511,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             for (int i = tid; i < n; i += nt) sr[i] = csr_row(A.cs_ptr, A.cs_col, A.cs_s, i, sqn) - sb[i];
             __syncthreads();
             add_fnl(A, sqn, sr);
-            cta_blocked_solve<T>(cLc, cLr, cDi, n, b, A.nblk, sr, tmp);
+            cta_blocked_solve<T>(cLc, cLr, cDi, n, b, A.nblk, sr, ysol, tmp);
             double dmax = 0.0, qmax = 0.0;
             for (int i = tid; i < n; i += nt) {
                 const double v = sqn[i] - sr[i];
@@ -446,12 +535,12 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
                 ++nref;
                 assemble_keff<T>(A, s, sqn, oLc, kt_out);
-                if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab)) {
+                if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
                     break;
                 }
-                cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi);
+                cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd);
                 __syncthreads();
                 cLc = oLc;
                 cLr = oLr;
@@ -485,8 +574,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     }
     // effective stiffness at the new state, its banded Cholesky factor and block inverses
     assemble_keff<T>(A, s, sq, oLc, kt_out);
-    const int bad = cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab);
-    if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi);
+    const int bad = cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg);
+    if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd);
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
         A.status[s] = s_stat;
@@ -503,14 +592,15 @@ __global__ void k_factor_M(int n, int b, const double* Mb, double* LMc, double* 
                            int* flag) {
     extern __shared__ double wndM[];
     const int nb = b + 1;
-    unsigned* tab = reinterpret_cast<unsigned*>(wndM + nb * nb);
+    double* stgM = wndM + nb * nb;
+    unsigned* tab = reinterpret_cast<unsigned*>(stgM + FSE_CHOL_PF * nb);
     fill_tri_table(b, tab);
     for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) {
         const int j = idx / nb, r = idx - j * nb, i = j + r;
         LMc[idx] = (i < n) ? Mb[(size_t)(b - r) * n + i] : 0.0;
     }
     __syncthreads();
-    const int bad = cta_band_cholesky<double>(LMc, LMr, LMinv, n, b, wndM, tab);
+    const int bad = cta_band_cholesky<double>(LMc, LMr, LMinv, n, b, wndM, tab, stgM);
     if (threadIdx.x == 0) *flag = bad;
 }
 
@@ -544,7 +634,7 @@ int launch_factor_M(fse_ctx* c) {
     const int nb = p.b + 1;
     int* flag = nullptr;
     if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
-    const size_t smem = (size_t)nb * nb * sizeof(double) + (size_t)(p.b * nb / 2 + 2) * 4;
+    const size_t smem = ((size_t)nb * nb + (size_t)FSE_CHOL_PF * nb) * sizeof(double) + (size_t)(p.b * nb / 2 + 2) * 4;
     cudaFuncSetAttribute(k_factor_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_factor_M<<<1, 256, smem, c->stream>>>(p.n, p.b, c->d.Mb, c->d.LMc, c->d.LMr, c->d.LMinv, flag);
     int h = 0;
@@ -558,7 +648,8 @@ size_t state_smem(const Params& p) {
     const int nb = p.b + 1;
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
     const size_t ntri = (size_t)p.b * nb / 2;
-    return (size_t)(6 * p.n + FSE_BLK) * 8 + ((ntri + 1) & ~(size_t)1) * 4 + (size_t)nb * nb * tsz;
+    const size_t wspan = std::max((size_t)nb * nb + (size_t)FSE_CHOL_PF * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
+    return (size_t)(6 * p.n + FSE_BLK) * 8 + ((ntri + 1) & ~(size_t)1) * 4 + (wspan + (size_t)p.n) * tsz;
 }
 
 static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
