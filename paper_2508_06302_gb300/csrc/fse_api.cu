@@ -119,7 +119,7 @@ static void free_ctx(fse_ctx* c) {
                     c->d.cs_B, c->d.kt_ptr, c->d.kt_col, c->d.kt_soff, c->d.kt_src, c->d.ke,
                     c->d.kt_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
                     c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
-                    c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
+                    c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.Rf, c->d.Rb, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
                     c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv, c->kry, c->kdot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -331,6 +331,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     }
     p.nnz_kt = (int)kcol.size();
     p.nblk = (n + FSE_BLK - 1) / FSE_BLK;
+    p.RECE = ((b + 3) & ~3) * FSE_BLK + FSE_BLK * FSE_BLK;
     p.ld = (p.P + 3) & ~3;
     // row groups: R chosen by the shared-memory wavefronts per 64-column pass of an entry
     // (4 for the X and V elements, RB / 16 for the broadcast record)
@@ -485,6 +486,9 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     A(&c->d.Lr, FSE_NBUF_F * (size_t)N * lb * tsz);
     A(&c->d.Linv, FSE_NBUF_F * Nn * tsz);
     A(&c->d.Dinv, FSE_NBUF_F * dsz);
+    const size_t rsz = (size_t)N * p.nblk * p.RECE * tsz;
+    A(&c->d.Rf, FSE_NBUF_F * rsz);
+    A(&c->d.Rb, FSE_NBUF_F * rsz);
     A(&c->d.X, sensz);
     A(&c->d.V, sensz);
     A(&c->d.Y, sensz);
@@ -538,6 +542,8 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     cudaMemsetAsync(c->d.iters, 0, (size_t)N * 4, st);
     cudaMemsetAsync(c->d.nref, 0, (size_t)N * 4, st);
     cudaMemsetAsync(c->d.flag, 0, 16, st);
+    cudaMemsetAsync(c->d.Rf, 0, FSE_NBUF_F * rsz, st);   // entries outside the band stay zero
+    cudaMemsetAsync(c->d.Rb, 0, FSE_NBUF_F * rsz, st);
     if (fse::make_tangent_maps(c) != FSE_OK) {
         rc = set_err(c, FSE_ECUDA, "TMA descriptor encoding failed");
         g_setup_err = c->err;

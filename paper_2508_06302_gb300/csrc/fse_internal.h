@@ -91,6 +91,11 @@ struct Dev {
     void* Lr = nullptr;
     void* Linv = nullptr;    // NBUF x N x n
     void* Dinv = nullptr;    // NBUF x N x nblk x 32 x 32
+    // per 32-row block, contiguous records for the blocked tangent solves (NBUF x N x nblk x RECE):
+    // forward Rf = [L(i0 + r, i0 - b + c) at c * 32 + r, c < bpad | Dinv^T], backward
+    // Rb = [L(i0 + 32 + c, i0 + r) at c * 32 + r | Dinv]; entries outside the band stay zero
+    void* Rf = nullptr;
+    void* Rb = nullptr;
     // tangents (sensitivity precision)
     void* X = nullptr;       // N x n x ld (columns P..ld-1 are zero padding)
     void* V = nullptr;
@@ -117,6 +122,7 @@ struct Params {
     int kt_ld = 4;           // per-trajectory stride of the K_t values (nnz_kt rounded up to 4)
     int MK = 0;              // K_t entries of a pass's slice (max, a multiple of 4)
     int RWT = 0;             // ring rows of the blocked solves (power of two >= b + 32)
+    int RECE = 0;            // elements of one block record of Rf / Rb: bpad * 32 + 32 * 32
     double tol = 0;
     size_t smem_state = 0, smem_rhs = 0, smem_trsm = 0;
 };

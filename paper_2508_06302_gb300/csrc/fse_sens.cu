@@ -21,12 +21,12 @@ namespace fse {
 
 struct SensArgs {
     int n, b, P, ld, kt_ld, nblk, RW, RWT;
-    int ng, ME, RB, MK;
+    int ng, ME, RB, MK, RECE;
     double a2c;
     const int* kt_slot;
     int* err;   // set when a pipeline wait gives up
     const void *g_rec, *g_rr, *g_info, *g_pass, *kt_val, *romega;
-    const void *Lc, *Lr, *Dinv;
+    const void *Lc, *Lr, *Dinv, *Rf, *Rb;
     void *X, *V, *Y;
 };
 
@@ -554,6 +554,194 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_trsm(SensArgs A
     }
 }
 
+// 16-byte load/store of 16 / sizeof(T) consecutive elements (one vector per lane)
+template <typename T>
+__device__ __forceinline__ void ldv(const T* p, T v[16 / sizeof(T)]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    } else {
+        const double2 x = *reinterpret_cast<const double2*>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const T v[16 / sizeof(T)]) {
+    if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+
+// 16-byte shared-memory vector load/store at a 32-bit shared address
+template <typename T>
+__device__ __forceinline__ void lds_vec(unsigned a, T v[16 / sizeof(T)]) {
+    if constexpr (sizeof(T) == 4)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                     : "r"(a));
+    else
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+}
+template <typename T>
+__device__ __forceinline__ void sts_vec(unsigned a, const T v[16 / sizeof(T)]) {
+    if constexpr (sizeof(T) == 4)
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                     "f"(v[3])
+                     : "memory");
+    else
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(v[0]), "d"(v[1]) : "memory");
+}
+
+// Blocked banded substitution with 8 x EL register tiles (b <= 96): one CTA = one trajectory
+// x CW = 64 EL directions (256 in FP32, 128 in FP64), 8 warps = 4 row groups of 8 rows x 2
+// column halves.  Each shared-memory read of a solved row feeds 8 rows.  The factor of the
+// block (its band tile and the diagonal-block inverse, one contiguous record written by the
+// state kernel) comes by one bulk copy per block, double-buffered on mbarriers; the next
+// block's right-hand side rows are loaded into registers while the current block computes.
+//  FWD: y_B = Dinv_B (rhs_B - L_{B,<} y_<)      record Rf = [L(i0 + r, i0 - b + c) | Dinv^T]
+//  BWD: x_B = Dinv_B^T (y_B - L_{>,B}^T x_>)    record Rb = [L(i0 + 32 + c, i0 + r) | Dinv]
+//       then X <- x, V <- 2/D (x - X) - V.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
+    constexpr int EL = 16 / sizeof(T);             // columns per lane
+    constexpr int CW = 64 * EL;                    // columns per CTA
+    constexpr int RT = 8;                          // rows per thread
+    const int n = A.n, b = A.b, ld = A.ld, RM = A.RWT - 1, RECE = A.RECE, nblk = A.nblk;
+    const int s = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rg = warp & 3, cg = warp >> 2;
+    const int r0 = RT * rg;                        // first row of this thread in the block
+    const int cl = cg * (CW / 2) + EL * lane;      // first column of this thread in the tile
+    const int t = blockIdx.x * CW + cl;            // global column
+    const bool tok = t < ld;
+    __shared__ __align__(8) unsigned long long bar[2];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* ring = reinterpret_cast<T*>(smraw);                        // RWT x CW  solved rows
+    T* stg = ring + (size_t)A.RWT * CW;                           // 32 x CW   block before Dinv
+    T* rec0 = stg + (size_t)FSE_BLK * CW;                         // 2 records
+    T* rec1 = rec0 + RECE;
+    // shared memory is read and written through explicit 32-bit shared addresses
+    constexpr unsigned TS = sizeof(T);
+    const unsigned sRing = smem_addr(ring) + cl * TS, sStg = smem_addr(stg), sRec0 = smem_addr(rec0);
+    const unsigned recb = (unsigned)RECE * TS;
+    const T* R = reinterpret_cast<const T*>(FWD ? A.Rf : A.Rb) + (size_t)s * nblk * RECE;
+    const size_t base = (size_t)s * n * ld;
+    T* Y = reinterpret_cast<T*>(A.Y) + base;
+    T* X = reinterpret_cast<T*>(A.X) + base;
+    T* V = reinterpret_cast<T*>(A.V) + base;
+    const T a2 = T(A.a2c);
+    const int dofs = RECE - FSE_BLK * FSE_BLK;
+    const unsigned recbytes = (unsigned)(RECE * sizeof(T));
+    auto blk = [&](int q) { return FWD ? q : nblk - 1 - q; };
+    auto load_rows = [&](const T* src, int B, T out[RT][EL]) {
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) {
+            const int i = B * FSE_BLK + r0 + rr;
+            if (i < n && tok) {
+                ldv(src + (size_t)i * ld + t, out[rr]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < EL; ++e) out[rr][e] = T(0);
+            }
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_tx(&bar[0], recbytes);
+        bulk_g2s(rec0, R + (size_t)blk(0) * RECE, recbytes, &bar[0]);
+    }
+    T ynext[RT][EL];
+    load_rows(Y, blk(0), ynext);
+    bool ok = true;
+    for (int q = 0; q < nblk; ++q) {
+        const int B = blk(q), i0 = B * FSE_BLK, buf = q & 1;
+        // the record buffer of block q + 1 was last read by block q - 1 (finished at its last barrier)
+        if (threadIdx.x == 0 && q + 1 < nblk) {
+            mbar_arrive_tx(&bar[buf ^ 1], recbytes);
+            bulk_g2s(buf ? rec0 : rec1, R + (size_t)blk(q + 1) * RECE, recbytes, &bar[buf ^ 1]);
+        }
+        T acc[RT][EL], xo[RT][EL], vo[RT][EL];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+            for (int e = 0; e < EL; ++e) acc[rr][e] = ynext[rr][e];
+        if (!FWD) {
+            load_rows(X, B, xo);
+            load_rows(V, B, vo);
+        }
+        if (q + 1 < nblk) load_rows(Y, blk(q + 1), ynext);
+        const bool wok = mbar_wait(&bar[buf], (q >> 1) & 1, A.err);
+        const unsigned sL = sRec0 + (buf ? recb : 0u) + r0 * TS;     // this thread's 8 rows of the record
+        // band part: rows of earlier (FWD) or later (BWD) blocks from the ring
+        const int c0 = FWD ? max(0, b - i0) : 0;
+        const int c1 = FWD ? b : min(b, n - (i0 + FSE_BLK));
+        for (int c = c0; c < c1; ++c) {
+            const int rowg = FWD ? (i0 - b + c) : (i0 + FSE_BLK + c);
+            T xv[EL], lv[RT];
+            lds_vec<T>(sRing + (unsigned)(rowg & RM) * (CW * TS), xv);
+#pragma unroll
+            for (int k = 0; k < RT / EL; ++k) lds_vec<T>(sL + (c * FSE_BLK + EL * k) * TS, lv + EL * k);
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) acc[rr][e] -= lv[rr] * xv[e];
+        }
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) sts_vec<T>(sStg + ((r0 + rr) * CW + cl) * TS, acc[rr]);
+        ok = __syncthreads_and(wok) != 0;   // the whole CTA leaves together if a wait gave up
+        if (!ok) {
+            if (threadIdx.x == 0 && q + 1 < nblk) mbar_wait(&bar[buf ^ 1], ((q + 1) >> 1) & 1, A.err);
+            break;
+        }
+        // diagonal block: out_r = sum_k D'[k][r] stg_k with D' = Dinv^T (FWD) or Dinv (BWD)
+        T out[RT][EL];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+            for (int e = 0; e < EL; ++e) out[rr][e] = T(0);
+        const unsigned sD = sL + dofs * TS;
+#pragma unroll 4
+        for (int k = 0; k < FSE_BLK; ++k) {
+            T tv[EL], dv[RT];
+            lds_vec<T>(sStg + (k * CW + cl) * TS, tv);
+#pragma unroll
+            for (int j = 0; j < RT / EL; ++j) lds_vec<T>(sD + (k * FSE_BLK + EL * j) * TS, dv + EL * j);
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) out[rr][e] += dv[rr] * tv[e];
+        }
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) {
+            const int i = i0 + r0 + rr;
+            sts_vec<T>(sRing + (unsigned)(i & RM) * (CW * TS), out[rr]);
+            if (i < n && tok) {
+                const size_t o = (size_t)i * ld + t;
+                if (FWD) {
+                    stv(Y + o, out[rr]);
+                } else {
+                    T vn[EL];
+#pragma unroll
+                    for (int e = 0; e < EL; ++e) vn[e] = a2 * (out[rr][e] - xo[rr][e]) - vo[rr][e];
+                    stv(X + o, out[rr]);
+                    stv(V + o, vn);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // X_0 = [I 0 0], V_0 = [0 I 0], zero padding columns
 template <typename T>
 __global__ void k_sens_init(int N, int n, int ld, T* X, T* V) {
@@ -641,6 +829,10 @@ static void rhs_launch(fse_ctx* c, const SensArgs& A, cudaStream_t st) {
 
 size_t trsm_smem(const Params& p) {
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
+    if (p.b <= 96) {   // k_trsm8: ring + staging block of CW = 64 x 16 / tsz columns + 2 records
+        const size_t cw = 64 * (16 / tsz);
+        return ((size_t)p.RWT * cw + (size_t)FSE_BLK * cw + 2 * (size_t)p.RECE) * tsz;
+    }
     return ((size_t)p.RWT * 128 + 2 * ((size_t)((p.b + 3) & ~3) * 32 + 1024)) * tsz;
 }
 
@@ -662,6 +854,19 @@ static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t s
             case 3: rhs_launch<T, 3>(c, A, st); break;
             default: rhs_launch<T, 4>(c, A, st); break;
         }
+    } else if (p.b <= 96) {
+        static bool attr8 = false;
+        if (!attr8) {
+            cudaFuncSetAttribute(k_trsm8<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(k_trsm8<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            attr8 = true;
+        }
+        constexpr int CW = 64 * (16 / (int)sizeof(T));
+        dim3 g((p.P + CW - 1) / CW, p.N);
+        if (phase == 1)
+            k_trsm8<T, true><<<g, 256, p.smem_trsm, st>>>(A);
+        else
+            k_trsm8<T, false><<<g, 256, p.smem_trsm, st>>>(A);
     } else {
         dim3 g((p.P + 127) / 128, p.N);
         const bool small = p.b <= 96;   // factor tile of b x 32 spread over 256 threads
@@ -704,6 +909,7 @@ void launch_sens_phase(fse_ctx* c, int k, double w, int phase, cudaStream_t st) 
     A.nblk = p.nblk;
     A.RW = p.RW;
     A.RWT = p.RWT;
+    A.RECE = p.RECE;
     A.a2c = 2.0 / Dl;
     A.ng = p.ng;
     A.ME = p.ME;
@@ -724,6 +930,9 @@ void launch_sens_phase(fse_ctx* c, int k, double w, int phase, cudaStream_t st) 
     A.Lc = (const char*)c->d.Lc + f * fsz;                             // factor of K_eff(q_{k+1})
     A.Lr = (const char*)c->d.Lr + f * fsz;
     A.Dinv = (const char*)c->d.Dinv + f * dsz;
+    const size_t rsz = (size_t)p.N * p.nblk * p.RECE * tsz;
+    A.Rf = (const char*)c->d.Rf + f * rsz;
+    A.Rb = (const char*)c->d.Rb + f * rsz;
     A.X = c->d.X;
     A.V = c->d.V;
     A.Y = c->d.Y;

@@ -91,7 +91,8 @@ __device__ void fill_tri_table(int b, unsigned* tab) {
 #define FSE_CHOL_PF 8
 
 template <typename T>
-__device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab, T* stg) {
+__device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab, T* stg,
+                                 T* Rf = nullptr, T* Rb = nullptr, int RECE = 0) {
     constexpr int PF = FSE_CHOL_PF;
     const int nb = b + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -143,7 +144,18 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
             const int r = tid;
             const T v = (j + r < n) ? (r == 0 ? ljj : colj[r] * inv) : T(0);
             Ac[(size_t)j * nb + r] = v;
-            if (j + r < n) Lr[(size_t)(j + r) * nb + (b - r)] = v;
+            if (j + r < n) {
+                const int i = j + r;
+                Lr[(size_t)i * nb + (b - r)] = v;
+                if (Rf) {
+                    // forward record of the block of row i: L(i, j) left of the block
+                    const int i0 = i & ~(FSE_BLK - 1);
+                    if (j < i0) Rf[(size_t)(i >> 5) * RECE + (j - i0 + b) * FSE_BLK + (i - i0)] = v;
+                    // backward record of the block of column j: L(i, j) below the block
+                    const int j0 = j & ~(FSE_BLK - 1), cb = i - j0 - FSE_BLK;
+                    if (cb >= 0) Rb[(size_t)(j >> 5) * RECE + cb * FSE_BLK + (j - j0)] = v;
+                }
+            }
             if (r == 0) {
                 Linv[j] = inv;
                 for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
@@ -160,7 +172,8 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
 // inverses of the 32 x 32 diagonal blocks of L (one warp per block, one lane per column);
 // the block's lower triangle is first copied to the warp's shared tile
 template <typename T>
-__device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int nblk, T* Dinv, T* tiles) {
+__device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int nblk, T* Dinv, T* tiles,
+                                  T* Rf = nullptr, T* Rb = nullptr, int RECE = 0) {
     const int nb = b + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     T* Lt = tiles + (size_t)warp * (FSE_BLK * FSE_BLK + FSE_BLK);   // [i][j] j < i, then 1/L_ii
@@ -184,6 +197,16 @@ __device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int 
         T* D = Dinv + (size_t)B * FSE_BLK * FSE_BLK;
 #pragma unroll
         for (int i = 0; i < FSE_BLK; ++i) D[i * FSE_BLK + lane] = z[i];
+        if (Rf) {
+            const int dofs = RECE - FSE_BLK * FSE_BLK;
+            T* DT = Rf + (size_t)B * RECE + dofs;   // forward record: Dinv^T
+            T* Db = Rb + (size_t)B * RECE + dofs;   // backward record: Dinv
+#pragma unroll
+            for (int i = 0; i < FSE_BLK; ++i) {
+                DT[lane * FSE_BLK + i] = z[i];
+                Db[i * FSE_BLK + lane] = z[i];
+            }
+        }
     }
     __syncwarp();
 }
@@ -210,6 +233,8 @@ struct StateArgs {
     double *q, *u, *a;
     const void *cLc, *cLr, *cLinv, *cDinv;   // chord factor (regular steps)
     void *oLc, *oLr, *oLinv, *oDinv;         // factor of K_eff at the new state
+    void *oRf, *oRb;                         // its block records for the tangent solves
+    int RECE;
     int *status, *iters, *nref;
 };
 
@@ -457,6 +482,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     T* oLr = reinterpret_cast<T*>(A.oLr) + foff;
     T* oLi = reinterpret_cast<T*>(A.oLinv) + off;
     T* oDi = reinterpret_cast<T*>(A.oDinv) + doff;
+    T* oRf = reinterpret_cast<T*>(A.oRf) + (size_t)s * A.nblk * A.RECE;
+    T* oRb = reinterpret_cast<T*>(A.oRb) + (size_t)s * A.nblk * A.RECE;
     T* kt_out = reinterpret_cast<T*>(A.kt_out) + (size_t)s * A.kt_ld;
     fill_tri_table(b, tab);
     if (tid == 0) {
@@ -535,12 +562,12 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
                 ++nref;
                 assemble_keff<T>(A, s, sqn, oLc, kt_out);
-                if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg)) {
+                if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
                     break;
                 }
-                cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd);
+                cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
                 __syncthreads();
                 cLc = oLc;
                 cLr = oLr;
@@ -574,8 +601,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     }
     // effective stiffness at the new state, its banded Cholesky factor and block inverses
     assemble_keff<T>(A, s, sq, oLc, kt_out);
-    const int bad = cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg);
-    if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd);
+    const int bad = cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE);
+    if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
         A.status[s] = s_stat;
@@ -716,6 +743,10 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.oLr = (char*)c->d.Lr + fo * fsz;
     A.oLinv = (char*)c->d.Linv + fo * vsz;
     A.oDinv = (char*)c->d.Dinv + fo * dsz;
+    const size_t rsz = (size_t)p.N * p.nblk * p.RECE * tsz;
+    A.oRf = (char*)c->d.Rf + fo * rsz;
+    A.oRb = (char*)c->d.Rb + fo * rsz;
+    A.RECE = p.RECE;
     A.status = c->d.status;
     A.iters = c->d.iters;
     A.nref = c->d.nref;
