@@ -45,6 +45,8 @@ def parse():
                     help="small case: N trajectories (H = (N-1)//2) instead of the workload's")
     ap.add_argument("--newmark-steps", type=int, default=0,
                     help="small case: integrate only the first K Newmark steps of the period")
+    ap.add_argument("--points", type=int, default=0,
+                    help="also time K converged continuation points (secant predictor, chord corrector)")
     return ap.parse_args()
 
 
@@ -221,6 +223,34 @@ def cpu_baseline(wl, seconds):
                       % (done, wl.name, el)}
 
 
+def continuation_points(fse, ctx, wl, K):
+    """K + 1 points of the w_1 sweep from 0.90 w_n1 in steps of 0.002 w_n1: the first converged
+    from the discrete linear response (not counted), then K points with the secant predictor and
+    the chord corrector (one Jacobian per point, GMRES on the structured products for the outer
+    solve), each accepted at ||R|| <= 1e-10 ||Z|| (FP64 residual)."""
+    import dataclasses
+    w_n1 = wl.model.omega_n1
+    omegas = w_n1 * (0.90 + 0.002 * np.arange(K + 1))
+    Z0 = initial_coeffs(dataclasses.replace(wl, omega1=float(omegas[0])))
+    ctx.set_steps(0)
+    ctx.profile(False)
+    Z, pts, rc = fse.fse_continue(ctx, omegas, Z0, rel_tol=1e-10, max_newton=40, chord=True)
+    timed = pts[1:]
+    tot_ms = sum(p["ms"] for p in timed)
+    lin = ctx.linear_stats()
+    return {"points": K, "points_per_s": K / (tot_ms / 1e3) if tot_ms > 0 else None,
+            "ms_per_point": [round(p["ms"], 1) for p in timed],
+            "newton_iters": [p["newton_iters"] for p in timed],
+            "jacobian_evals_per_point": 1,
+            "residual_evals": [p["evals"] - 1 for p in timed],
+            "rel_res": [p["res"] / p["znorm"] for p in timed],
+            "status": [p["status"] for p in timed], "rc": rc,
+            "first_point": {"ms": round(pts[0]["ms"], 1), "newton_iters": pts[0]["newton_iters"],
+                            "status": pts[0]["status"]},
+            "last_gmres": {"iters": lin[0], "rel_res": lin[1]},
+            "omega1_over_wn1": [round(float(w / w_n1), 4) for w in omegas]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -382,6 +412,9 @@ def main():
                 "traffic": recorded_traffic("k_" + kname, wl.name),
                 "peak_source": ("%s of %s (HBM copy)" % (hbm_peak, src)) if kk["bound"] == "hbm" else
                 ("152 SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (lanes, sm_mhz))}
+    cont = None
+    if args.points > 0:
+        cont = continuation_points(fse, ctx, wl, args.points)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, args.cpu_seconds)
@@ -405,6 +438,8 @@ def main():
         "gpu_launches": args.steps * (4 * n_newmark + 6),
         "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "peaks_source": src,
     }
+    if cont is not None:
+        line["continuation"] = cont
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -169,6 +169,116 @@ __device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, co
     return bad;
 }
 
+// Banded Cholesky with the window in registers (T = float, b <= 127).  Thread t owns rows
+// [p R, (p + 1) R) of window slot t mod nb, p = t / nb < floor(256 / nb), R = ceil(nb / parts).
+// Step j: the owners of column j publish it to a shared buffer (two buffers, alternating), one
+// barrier, then every thread applies A_ik -= A_ij A_kj / A_jj to its slice from that read-only
+// buffer, threads < nb write column j of L out, and the owners of slot j take column j + nb
+// from the cp.async staging ring.  One barrier per column; the window never aliases itself.
+template <typename T, int MAXR>
+__device__ int cta_band_cholesky_reg(T* Ac, T* Lr, T* Linv, int n, int b, T* colbuf, T* stg, T* Rf, T* Rb,
+                                     int RECE) {
+    constexpr int PF = FSE_CHOL_PF;
+    const int nb = b + 1;
+    const int tid = threadIdx.x;
+    const int parts = blockDim.x / nb;                 // >= 2 for nb <= 128
+    const int R = (nb + parts - 1) / parts;            // <= MAXR
+    const int myslot = tid % nb, mypart = tid / nb;
+    const bool owner = mypart < parts;
+    const int rr0 = mypart * R;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    T val[MAXR];
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+        const int rr = rr0 + m;
+        val[m] = (owner && m < R && rr < nb && myslot < n) ? Ac[(size_t)myslot * nb + rr] : T(0);
+    }
+    auto issue = [&](int col) {   // stage column col into stg[col % PF]
+        if (col < n && tid < nb) cp_async_elem(stg + (col % PF) * nb + tid, Ac + (size_t)col * nb + tid);
+        cp_async_commit();
+    };
+    for (int c = 0; c < PF - 1; ++c) issue(nb + c);
+    int slot = 0;   // window slot of column j (= j mod nb)
+    for (int j = 0; j < n; ++j, slot = (slot + 1 == nb) ? 0 : slot + 1) {
+        T* cb = colbuf + (j & 1) * nb;
+        if (owner && myslot == slot) {
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m)
+                if (m < R && rr0 + m < nb) cb[rr0 + m] = val[m];
+        }
+        cp_async_wait<PF - 2>();   // this thread's entry of column j + nb has landed
+        __syncthreads();
+        issue(j + nb + PF - 1);    // into the staging slot read at step j - 1
+        const T piv = cb[0];
+        if (!(piv > T(0)) || !isfinite((double)piv)) {
+            if (tid == 0) bad = 1;
+            break;
+        }
+        const T ljj = sqrt(piv);
+        const T inv = T(1) / ljj;
+        const T inv2 = inv * inv;
+        int cc = myslot - slot;
+        cc = cc < 0 ? cc + nb : cc;            // column j + cc of this thread's slot
+        if (owner && cc >= 1 && j + cc < n) {
+            const T g = cb[cc] * inv2;
+            const int lim = b - cc;            // rows rr <= b - cc of that column are in the band of j
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m) {
+                const int rr = rr0 + m;
+                if (m < R && rr <= lim) val[m] -= cb[cc + rr] * g;
+            }
+        }
+        // column j of L
+        if (tid < nb) {
+            const int r = tid;
+            const T v = (j + r < n) ? (r == 0 ? ljj : cb[r] * inv) : T(0);
+            Ac[(size_t)j * nb + r] = v;
+            if (j + r < n) {
+                const int i = j + r;
+                Lr[(size_t)i * nb + (b - r)] = v;
+                if (Rf) {
+                    const int i0 = i & ~(FSE_BLK - 1);
+                    if (j < i0) Rf[(size_t)(i >> 5) * RECE + (j - i0 + b) * FSE_BLK + (i - i0)] = v;
+                    const int j0 = j & ~(FSE_BLK - 1), cbk = i - j0 - FSE_BLK;
+                    if (cbk >= 0) Rb[(size_t)(j >> 5) * RECE + cbk * FSE_BLK + (j - j0)] = v;
+                }
+            }
+            if (r == 0) {
+                Linv[j] = inv;
+                for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
+            }
+        }
+        // the owners of slot j take column j + nb
+        if (owner && cc == 0) {
+            const int jn = j + nb;
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m) {
+                const int rr = rr0 + m;
+                if (m < R && rr < nb) val[m] = (jn < n) ? stg[(jn % PF) * nb + rr] : T(0);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    return bad;
+}
+
+// FP32 factors with 2 <= b + 1 <= 128 use the register window; FP64 and wider bands the shared one
+template <typename T>
+__device__ int band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab, T* stg, T* Rf,
+                             T* Rb, int RECE) {
+    if constexpr (sizeof(T) == 4) {
+        const int nb = b + 1;
+        if (nb >= 2 && nb <= 128 && blockDim.x == 256) {
+            const int parts = 256 / nb, R = (nb + parts - 1) / parts;
+            if (R <= 16) return cta_band_cholesky_reg<T, 16>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
+            return cta_band_cholesky_reg<T, 64>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
+        }
+    }
+    return cta_band_cholesky<T>(Ac, Lr, Linv, n, b, wnd, tab, stg, Rf, Rb, RECE);
+}
+
 // inverses of the 32 x 32 diagonal blocks of L (one warp per block, one lane per column);
 // the block's lower triangle is first copied to the warp's shared tile
 template <typename T>
@@ -562,7 +672,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
                 ++nref;
                 assemble_keff<T>(A, s, sqn, oLc, kt_out);
-                if (cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE)) {
+                if (band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
                     break;
@@ -601,7 +711,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     }
     // effective stiffness at the new state, its banded Cholesky factor and block inverses
     assemble_keff<T>(A, s, sq, oLc, kt_out);
-    const int bad = cta_band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE);
+    const int bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE);
     if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
