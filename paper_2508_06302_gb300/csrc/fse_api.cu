@@ -426,7 +426,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.smem_trsm = fse::trsm_smem(p);
     const size_t lim = 220 * 1024;
     if (b > FSE_MAX_BAND || p.smem_state > lim || p.smem_rhs > lim || p.smem_trsm > lim ||
-        ((size_t)nb * nb + (size_t)8 * nb) * sizeof(double) + (size_t)(b * nb / 2 + 2) * 4 > lim) {
+        (size_t)(nb + 9) * nb * sizeof(double) > lim) {
         free_ctx(c);
         return set_err(nullptr, FSE_EINVAL, "n or half-bandwidth too large for the on-chip working set");
     }

@@ -78,159 +78,175 @@ __global__ void k_build_ops(int nnz, double cm, double cd, double cb, const doub
 // banded Cholesky inside one CTA: column band Ac (global, in place) -> Lc, Lr, Linv
 // ----------------------------------------------------------------------------
 
-// pairs (cc, rr), cc in [1, b], rr in [0, b - cc]: entries of the trailing triangle
-__device__ void fill_tri_table(int b, unsigned* tab) {
-    for (int cc = 1; cc <= b; ++cc) {
-        const int base = (cc - 1) * (2 * b - cc + 2) / 2;   // sum_{c'<cc} (b - c' + 1)
-        for (int rr = threadIdx.x; rr <= b - cc; rr += blockDim.x)
-            tab[base + rr] = ((unsigned)cc << 16) | (unsigned)rr;
-    }
-}
-
 // columns of the band staged ahead of the Cholesky window (cp.async ring)
 #define FSE_CHOL_PF 8
 
+// Banded Cholesky with a warp-cooperative trailing update.  The window holds the nb columns
+// j..j+b in nb + 1 shared slots (column c in slot c mod (nb + 1)).  Step j, between two barriers:
+//  (a) threads r < nb write column j - 1 of L out of its slot, refill that slot with column
+//      j + nb from the cp.async staging ring (entry r was staged by thread r) and stage
+//      column j + nb + PF - 1;
+//  (b) warp w updates columns j + cc, cc = w + 1, w + 1 + 8, ..., with lanes over the rows:
+//      A_(j+cc+rr, j+cc) -= A_(j+cc+rr, j) A_(j+cc, j) / A_(j, j), rr <= b - cc.
+// (a) and (b) touch different slots, so one barrier per column suffices.
 template <typename T>
-__device__ int cta_band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab, T* stg,
-                                 T* Rf = nullptr, T* Rb = nullptr, int RECE = 0) {
+__device__ int cta_band_cholesky_w(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, T* stg, T* Rf, T* Rb, int RECE) {
     constexpr int PF = FSE_CHOL_PF;
-    const int nb = b + 1;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int ntri = b * (b + 1) / 2;
+    const int nb = b + 1, ns = nb + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     __shared__ int bad;
     if (tid == 0) bad = 0;
-    for (int idx = tid; idx < nb * nb; idx += nt) {
-        const int c = idx / nb;
+    for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+        const int c = idx / nb;   // column c starts in slot c
         wnd[idx] = (c < n) ? Ac[(size_t)c * nb + (idx - c * nb)] : T(0);
     }
-    // the column entering the window at step j (column j + nb) is staged PF - 1 steps ahead;
-    // thread r copies and later reads entry r of every staged column
-    auto issue = [&](int col) {
-        if (col < n && tid < nb) cp_async_elem(stg + (col % PF) * nb + tid, Ac + (size_t)col * nb + tid);
+    auto issue = [&](int col) {   // thread tid < nb stages entry tid of column col
+        if (col < n) cp_async_elem(stg + (col % PF) * nb + tid, Ac + (size_t)col * nb + tid);
         cp_async_commit();
     };
-    for (int c = 0; c < PF - 1; ++c) issue(nb + c);
+    if (tid < nb)
+        for (int c = 0; c < PF - 1; ++c) issue(nb + c);
+    // write column jp of L (its pivot 1/L_jj = inv, L_jj = ljj) from slot colp; thread r < nb
+    auto write_col = [&](int jp, const T* colp, T ljj, T inv) {
+        const int r = tid;
+        const T v = (jp + r < n) ? (r == 0 ? ljj : colp[r] * inv) : T(0);
+        Ac[(size_t)jp * nb + r] = v;
+        if (jp + r < n) {
+            const int i = jp + r;
+            Lr[(size_t)i * nb + (b - r)] = v;
+            if (Rf) {
+                const int i0 = i & ~(FSE_BLK - 1);
+                if (jp < i0) Rf[(size_t)(i >> 5) * RECE + (jp - i0 + b) * FSE_BLK + (i - i0)] = v;
+                const int j0 = jp & ~(FSE_BLK - 1), cbk = i - j0 - FSE_BLK;
+                if (cbk >= 0) Rb[(size_t)(jp >> 5) * RECE + cbk * FSE_BLK + (jp - j0)] = v;
+            }
+        }
+        if (r == 0) {
+            Linv[jp] = inv;
+            for (int c = 0; c < b - jp; ++c) Lr[(size_t)jp * nb + c] = T(0);
+        }
+    };
     __syncthreads();
-    int slot = 0;   // window slot of column j (= j mod nb)
-    for (int j = 0; j < n; ++j, slot = (slot + 1 == nb) ? 0 : slot + 1) {
-        issue(j + nb + PF - 1);
-        T* colj = wnd + slot * nb;
+    T ljj_prev = T(0), inv_prev = T(0);
+    int slot = 0;   // slot of column j
+    int j = 0;
+    for (; j < n; ++j) {
+        const T* colj = wnd + slot * nb;
         const T piv = colj[0];
         if (!(piv > T(0)) || !isfinite((double)piv)) {
             if (tid == 0) bad = 1;
-            __syncthreads();
             break;
         }
         const T ljj = sqrt(piv);
         const T inv = T(1) / ljj;
         const T inv2 = inv * inv;
-        // trailing update with the unscaled column: A_ik -= A_ij A_kj / A_jj
-        const int ccmax = n - 1 - j;
-        for (int idx = tid; idx < ntri; idx += nt) {
-            const unsigned pr = tab[idx];
-            const int cc = (int)(pr >> 16), rr = (int)(pr & 0xffffu);
-            if (cc <= ccmax) {
-                int sc = slot + cc;
-                sc = (sc >= nb) ? sc - nb : sc;
-                wnd[sc * nb + rr] -= colj[cc + rr] * colj[cc] * inv2;
-            }
+        const int sp = (slot == 0) ? ns - 1 : slot - 1;   // slot of column j - 1 = slot of column j + nb
+        if (tid < nb) {
+            T* colp = wnd + sp * nb;
+            if (j > 0) write_col(j - 1, colp, ljj_prev, inv_prev);
+            cp_async_wait<PF - 2>();   // entry tid of column j + nb has landed
+            const int jn = j + nb;
+            colp[tid] = (jn < n) ? stg[(jn % PF) * nb + tid] : T(0);
+            issue(jn + PF - 1);        // into the staging slot just read
         }
-        cp_async_wait<PF - 1>();   // this thread's entry of column j + nb has landed
-        __syncthreads();
-        // write column j of L out and move column j + nb into its slot (each thread owns
-        // the same entry r in all parts, so no barrier is needed between them)
-        const int jn = j + nb;
-        if (tid < nb) {   // nb <= blockDim.x: one entry per thread
-            const int r = tid;
-            const T v = (j + r < n) ? (r == 0 ? ljj : colj[r] * inv) : T(0);
-            Ac[(size_t)j * nb + r] = v;
-            if (j + r < n) {
-                const int i = j + r;
-                Lr[(size_t)i * nb + (b - r)] = v;
-                if (Rf) {
-                    // forward record of the block of row i: L(i, j) left of the block
-                    const int i0 = i & ~(FSE_BLK - 1);
-                    if (j < i0) Rf[(size_t)(i >> 5) * RECE + (j - i0 + b) * FSE_BLK + (i - i0)] = v;
-                    // backward record of the block of column j: L(i, j) below the block
-                    const int j0 = j & ~(FSE_BLK - 1), cb = i - j0 - FSE_BLK;
-                    if (cb >= 0) Rb[(size_t)(j >> 5) * RECE + cb * FSE_BLK + (j - j0)] = v;
-                }
-            }
-            if (r == 0) {
-                Linv[j] = inv;
-                for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
-            }
-            colj[r] = (jn < n) ? stg[(jn % PF) * nb + r] : T(0);
+        for (int cc = warp + 1; cc <= b; cc += nw) {
+            if (j + cc >= n) break;
+            int sc = slot + cc;
+            sc = (sc >= ns) ? sc - ns : sc;
+            T* colc = wnd + sc * nb;
+            const T g = colj[cc] * inv2;
+            for (int rr = lane; rr <= b - cc; rr += 32) colc[rr] -= colj[cc + rr] * g;
         }
         __syncthreads();
+        ljj_prev = ljj;
+        inv_prev = inv;
+        slot = (slot + 1 == ns) ? 0 : slot + 1;
     }
+    if (j == n && tid < nb) write_col(n - 1, wnd + ((slot == 0) ? ns - 1 : slot - 1) * nb, ljj_prev, inv_prev);
     cp_async_wait<0>();
     __syncthreads();
     return bad;
 }
 
-// Banded Cholesky with the window in registers (T = float, b <= 127).  Thread t owns rows
-// [p R, (p + 1) R) of window slot t mod nb, p = t / nb < floor(256 / nb), R = ceil(nb / parts).
-// Step j: the owners of column j publish it to a shared buffer (two buffers, alternating), one
-// barrier, then every thread applies A_ik -= A_ij A_kj / A_jj to its slice from that read-only
-// buffer, threads < nb write column j of L out, and the owners of slot j take column j + nb
-// from the cp.async staging ring.  One barrier per column; the window never aliases itself.
-template <typename T, int MAXR>
-__device__ int cta_band_cholesky_reg(T* Ac, T* Lr, T* Linv, int n, int b, T* colbuf, T* stg, T* Rf, T* Rb,
-                                     int RECE) {
+// Banded Cholesky with the window in registers (b + 1 <= 32 MAXK, nb <= 8 MAXS): warp w owns
+// window slots s = w, w + 8, ... (column c in slot c mod nb) and lane l the rows l + 32k of
+// them.  Step j: the owner warp of column j publishes it to a shared buffer (two, alternating),
+// one barrier, then every warp applies A_(c+rr, c) -= A_(c+rr, j) A_(c, j) / A_(j, j) to its
+// slots c = j + cc from that read-only buffer, threads < nb write column j of L out, and the
+// owner warp of slot j takes column j + nb from the cp.async staging ring.  Every warp has the
+// same work per step and the window never aliases the buffer it reads.
+template <typename T, int MAXS, int MAXK>
+__device__ int cta_band_cholesky_r(T* Ac, T* Lr, T* Linv, int n, int b, T* colbuf, T* stg, T* Rf, T* Rb,
+                                   int RECE) {
     constexpr int PF = FSE_CHOL_PF;
     const int nb = b + 1;
-    const int tid = threadIdx.x;
-    const int parts = blockDim.x / nb;                 // >= 2 for nb <= 128
-    const int R = (nb + parts - 1) / parts;            // <= MAXR
-    const int myslot = tid % nb, mypart = tid / nb;
-    const bool owner = mypart < parts;
-    const int rr0 = mypart * R;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     __shared__ int bad;
     if (tid == 0) bad = 0;
-    T val[MAXR];
+    T val[MAXS][MAXK];
+    int cc[MAXS];   // slot q holds column j + cc[q] (cc = 0: column j itself)
 #pragma unroll
-    for (int m = 0; m < MAXR; ++m) {
-        const int rr = rr0 + m;
-        val[m] = (owner && m < R && rr < nb && myslot < n) ? Ac[(size_t)myslot * nb + rr] : T(0);
+    for (int q = 0; q < MAXS; ++q) {
+        const int sl = warp + 8 * q;   // column sl at the start
+        cc[q] = sl < nb ? sl : -(1 << 28);   // slots past the window never become active
+#pragma unroll
+        for (int k = 0; k < MAXK; ++k) {
+            const int rr = lane + 32 * k;
+            val[q][k] = (sl < nb && sl < n && rr < nb) ? Ac[(size_t)sl * nb + rr] : T(0);
+        }
     }
-    auto issue = [&](int col) {   // stage column col into stg[col % PF]
-        if (col < n && tid < nb) cp_async_elem(stg + (col % PF) * nb + tid, Ac + (size_t)col * nb + tid);
+    auto issue = [&](int col) {   // thread tid < nb stages entry tid of column col
+        if (col < n) cp_async_elem(stg + (col % PF) * nb + tid, Ac + (size_t)col * nb + tid);
         cp_async_commit();
     };
-    for (int c = 0; c < PF - 1; ++c) issue(nb + c);
+    if (tid < nb)
+        for (int c = 0; c < PF - 1; ++c) issue(nb + c);
+    const unsigned sbuf = (unsigned)__cvta_generic_to_shared(colbuf);
     int slot = 0;   // window slot of column j (= j mod nb)
     for (int j = 0; j < n; ++j, slot = (slot + 1 == nb) ? 0 : slot + 1) {
         T* cb = colbuf + (j & 1) * nb;
-        if (owner && myslot == slot) {
+        const int ow = slot & 7, oq = slot >> 3;   // owner warp and its slot index
+        if (warp == ow) {
 #pragma unroll
-            for (int m = 0; m < MAXR; ++m)
-                if (m < R && rr0 + m < nb) cb[rr0 + m] = val[m];
+            for (int q = 0; q < MAXS; ++q)
+                if (q == oq) {
+#pragma unroll
+                    for (int k = 0; k < MAXK; ++k)
+                        if (lane + 32 * k < nb) cb[lane + 32 * k] = val[q][k];
+                }
         }
-        cp_async_wait<PF - 2>();   // this thread's entry of column j + nb has landed
+        if (tid < nb) cp_async_wait<PF - 2>();   // entry tid of column j + nb has landed
         __syncthreads();
-        issue(j + nb + PF - 1);    // into the staging slot read at step j - 1
+        if (tid < nb) issue(j + nb + PF - 1);     // into the staging slot read at step j - 1
         const T piv = cb[0];
-        if (!(piv > T(0)) || !isfinite((double)piv)) {
+        if (!(piv > T(0)) || !(piv < T(INFINITY))) {
             if (tid == 0) bad = 1;
             break;
         }
-        const T ljj = sqrt(piv);
-        const T inv = T(1) / ljj;
+        const T inv = rsqrtf(piv);   // 1 / L_jj (FP32 factor: refined by the FP64 residual)
+        const T ljj = piv * inv;
         const T inv2 = inv * inv;
-        int cc = myslot - slot;
-        cc = cc < 0 ? cc + nb : cc;            // column j + cc of this thread's slot
-        if (owner && cc >= 1 && j + cc < n) {
-            const T g = cb[cc] * inv2;
-            const int lim = b - cc;            // rows rr <= b - cc of that column are in the band of j
+        const unsigned cbs = sbuf + (unsigned)((j & 1) * nb) * 4u;
 #pragma unroll
-            for (int m = 0; m < MAXR; ++m) {
-                const int rr = rr0 + m;
-                if (m < R && rr <= lim) val[m] -= cb[cc + rr] * g;
+        for (int q = 0; q < MAXS; ++q) {
+            const int c = cc[q];
+            if (c >= 1 && c <= b && j + c < n) {
+                const unsigned a = cbs + (unsigned)(c + lane) * 4u;   // cb[c + lane]
+                T g;
+                asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(g) : "r"(cbs + (unsigned)c * 4u));
+                g *= inv2;
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k) {
+                    if (lane + 32 * k <= b - c) {
+                        T x;
+                        asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(x) : "r"(a + 128u * k));
+                        val[q][k] -= x * g;
+                    }
+                }
             }
+            cc[q] = (c == 0) ? b : c - 1;   // next step: column j + 1 + cc
         }
-        // column j of L
-        if (tid < nb) {
+        if (tid < nb) {   // column j of L
             const int r = tid;
             const T v = (j + r < n) ? (r == 0 ? ljj : cb[r] * inv) : T(0);
             Ac[(size_t)j * nb + r] = v;
@@ -249,34 +265,36 @@ __device__ int cta_band_cholesky_reg(T* Ac, T* Lr, T* Linv, int n, int b, T* col
                 for (int c = 0; c < b - j; ++c) Lr[(size_t)j * nb + c] = T(0);
             }
         }
-        // the owners of slot j take column j + nb
-        if (owner && cc == 0) {
+        if (warp == ow) {   // slot j takes column j + nb
             const int jn = j + nb;
 #pragma unroll
-            for (int m = 0; m < MAXR; ++m) {
-                const int rr = rr0 + m;
-                if (m < R && rr < nb) val[m] = (jn < n) ? stg[(jn % PF) * nb + rr] : T(0);
-            }
+            for (int q = 0; q < MAXS; ++q)
+                if (q == oq) {
+#pragma unroll
+                    for (int k = 0; k < MAXK; ++k) {
+                        const int rr = lane + 32 * k;
+                        if (rr < nb) val[q][k] = (jn < n) ? stg[(jn % PF) * nb + rr] : T(0);
+                    }
+                }
         }
     }
-    cp_async_wait<0>();
+    if (tid < nb) cp_async_wait<0>();
     __syncthreads();
     return bad;
 }
 
-// FP32 factors with 2 <= b + 1 <= 128 use the register window; FP64 and wider bands the shared one
+// FP32 factors with b + 1 <= 96 keep the window in registers; others use the shared window
 template <typename T>
-__device__ int band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, const unsigned* tab, T* stg, T* Rf,
-                             T* Rb, int RECE) {
+__device__ int band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, T* stg, T* Rf, T* Rb, int RECE) {
     if constexpr (sizeof(T) == 4) {
         const int nb = b + 1;
-        if (nb >= 2 && nb <= 128 && blockDim.x == 256) {
-            const int parts = 256 / nb, R = (nb + parts - 1) / parts;
-            if (R <= 16) return cta_band_cholesky_reg<T, 16>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
-            return cta_band_cholesky_reg<T, 64>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
+        if (nb >= 2 && blockDim.x == 256) {
+            if (nb <= 32) return cta_band_cholesky_r<T, 4, 1>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
+            if (nb <= 64) return cta_band_cholesky_r<T, 8, 2>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
+            if (nb <= 96) return cta_band_cholesky_r<T, 12, 3>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
         }
     }
-    return cta_band_cholesky<T>(Ac, Lr, Linv, n, b, wnd, tab, stg, Rf, Rb, RECE);
+    return cta_band_cholesky_w<T>(Ac, Lr, Linv, n, b, wnd, stg, Rf, Rb, RECE);
 }
 
 // inverses of the 32 x 32 diagonal blocks of L (one warp per block, one lane per column);
@@ -576,13 +594,11 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     extern __shared__ double sm[];
     double *sq = sm, *su = sq + n, *sa = su + n, *sqn = sa + n, *sb = sqn + n, *sr = sb + n;
     T* tmp = reinterpret_cast<T*>(sr + n);                // 32
-    unsigned* tab = reinterpret_cast<unsigned*>(sr + n + FSE_BLK);
-    const int ntri = b * (b + 1) / 2;
-    // Cholesky window (nb x nb) and staging ring (FSE_CHOL_PF x nb); the diagonal-block tiles
-    // of cta_diag_inverses reuse the same space once the factorisation is done
-    T* wnd = reinterpret_cast<T*>(tab + ((ntri + 1) & ~1));
-    T* stg = wnd + (size_t)nb * nb;
-    const size_t wspan = max((size_t)nb * nb + (size_t)FSE_CHOL_PF * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
+    // Cholesky window ((nb + 1) x nb) and staging ring (FSE_CHOL_PF x nb); the diagonal-block
+    // tiles of cta_diag_inverses reuse the same space once the factorisation is done
+    T* wnd = reinterpret_cast<T*>(sr + n + FSE_BLK);
+    T* stg = wnd + (size_t)(nb + 1) * nb;
+    const size_t wspan = max((size_t)(nb + 1 + FSE_CHOL_PF) * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
     T* ysol = wnd + wspan;                                // n: solve vector in the factor precision
     __shared__ int s_conv, s_stat;
     const size_t off = (size_t)s * n;
@@ -595,7 +611,6 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     T* oRf = reinterpret_cast<T*>(A.oRf) + (size_t)s * A.nblk * A.RECE;
     T* oRb = reinterpret_cast<T*>(A.oRb) + (size_t)s * A.nblk * A.RECE;
     T* kt_out = reinterpret_cast<T*>(A.kt_out) + (size_t)s * A.kt_ld;
-    fill_tri_table(b, tab);
     if (tid == 0) {
         s_stat = A.init ? 0 : A.status[s];
         s_conv = 0;
@@ -672,7 +687,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
                 ++nref;
                 assemble_keff<T>(A, s, sqn, oLc, kt_out);
-                if (band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE)) {
+                if (band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
                     break;
@@ -711,7 +726,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     }
     // effective stiffness at the new state, its banded Cholesky factor and block inverses
     assemble_keff<T>(A, s, sq, oLc, kt_out);
-    const int bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, tab, stg, oRf, oRb, A.RECE);
+    const int bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE);
     if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
@@ -729,15 +744,13 @@ __global__ void k_factor_M(int n, int b, const double* Mb, double* LMc, double* 
                            int* flag) {
     extern __shared__ double wndM[];
     const int nb = b + 1;
-    double* stgM = wndM + nb * nb;
-    unsigned* tab = reinterpret_cast<unsigned*>(stgM + FSE_CHOL_PF * nb);
-    fill_tri_table(b, tab);
+    double* stgM = wndM + (nb + 1) * nb;
     for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) {
         const int j = idx / nb, r = idx - j * nb, i = j + r;
         LMc[idx] = (i < n) ? Mb[(size_t)(b - r) * n + i] : 0.0;
     }
     __syncthreads();
-    const int bad = cta_band_cholesky<double>(LMc, LMr, LMinv, n, b, wndM, tab, stgM);
+    const int bad = cta_band_cholesky_w<double>(LMc, LMr, LMinv, n, b, wndM, stgM, nullptr, nullptr, 0);
     if (threadIdx.x == 0) *flag = bad;
 }
 
@@ -771,7 +784,7 @@ int launch_factor_M(fse_ctx* c) {
     const int nb = p.b + 1;
     int* flag = nullptr;
     if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
-    const size_t smem = ((size_t)nb * nb + (size_t)FSE_CHOL_PF * nb) * sizeof(double) + (size_t)(p.b * nb / 2 + 2) * 4;
+    const size_t smem = (size_t)(nb + 1 + FSE_CHOL_PF) * nb * sizeof(double);
     cudaFuncSetAttribute(k_factor_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_factor_M<<<1, 256, smem, c->stream>>>(p.n, p.b, c->d.Mb, c->d.LMc, c->d.LMr, c->d.LMinv, flag);
     int h = 0;
@@ -784,9 +797,8 @@ int launch_factor_M(fse_ctx* c) {
 size_t state_smem(const Params& p) {
     const int nb = p.b + 1;
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
-    const size_t ntri = (size_t)p.b * nb / 2;
-    const size_t wspan = std::max((size_t)nb * nb + (size_t)FSE_CHOL_PF * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
-    return (size_t)(6 * p.n + FSE_BLK) * 8 + ((ntri + 1) & ~(size_t)1) * 4 + (wspan + (size_t)p.n) * tsz;
+    const size_t wspan = std::max((size_t)(nb + 1 + FSE_CHOL_PF) * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
+    return (size_t)(6 * p.n + FSE_BLK) * 8 + (wspan + (size_t)p.n) * tsz;
 }
 
 static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
