@@ -33,6 +33,9 @@ CASES = {
     "chain5_d3": (lambda: I.chain(5, F=(1.0, 0.5, 0.3)), 3, [3, 5], [1, 2], 16,
                   [math.sqrt(2), math.sqrt(3)], 1.1, 1e-3),
     "chain4_d3_e1": (lambda: I.chain(4, F=(1.0,)), 3, [3, 3], [1, 1], 12, [0.37, 0.71], 1.2, 1e-3),
+    # d = 3 ACM plate (3 x 3 interior nodes, 3 seeded springs, three forcing frequencies)
+    "plate27_d3": (lambda: I.kirchhoff_plate(nx=4, ny=4, n_springs=3), 3, [3, 3], [1, 1], 16,
+                   [math.sqrt(2), math.sqrt(3)], 1.1, 1e-4),
 }
 
 
