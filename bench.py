@@ -45,6 +45,8 @@ def parse():
                     help="small case: N trajectories (H = (N-1)//2) instead of the workload's")
     ap.add_argument("--newmark-steps", type=int, default=0,
                     help="small case: integrate only the first K Newmark steps of the period")
+    ap.add_argument("--batch", action="store_true",
+                    help="also time the 8-point shell batch (N = 32..64) as one graph against one by one")
     ap.add_argument("--points", type=int, default=0,
                     help="also time K converged continuation points (secant predictor, chord corrector)")
     return ap.parse_args()
@@ -221,6 +223,34 @@ def cpu_baseline(wl, seconds):
     return {"value": done / el, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
             "sample": "%d traj-steps (with sensitivities) of one trajectory of %s in %.1f s"
                       % (done, wl.name, el)}
+
+
+def batch_points(fse, device):
+    """The 8 continuation points of uneven trajectory count (N = 32..64, H = (N-1)//2,
+    w_1 = w_n1 {0.95..1.3}) evaluated with their Jacobians as one captured CUDA graph,
+    against the same evaluations one context at a time (the graph is captured by an
+    untimed first call)."""
+    from paper_2508_06302_gb300 import inputs as I
+    wls = I.shell_batch_points()
+    ctxs = [fse.Context.from_workload(w, precision="mixed_fp32", device=device) for w in wls]
+    Zs = [initial_coeffs(w) for w in wls]
+    om = [w.omega1 for w in wls]
+    b = fse.Batch(ctxs, use_graph=True)
+    b.residual_jacobian(Zs, om, True)
+    t0 = time.perf_counter()
+    Rs, st, rc = b.residual_jacobian(Zs, om, True)
+    t_graph = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c, z, w in zip(ctxs, Zs, om):
+        c.residual_jacobian(z, w, True)
+    t_seq = time.perf_counter() - t0
+    ts = sum(w.N * w.S1 for w in wls)
+    b.close()
+    for c in ctxs:
+        c.close()
+    return {"points": len(wls), "trajectories": sum(w.N for w in wls), "status": [int(x) for x in st],
+            "graph_s": t_graph, "one_by_one_s": t_seq, "traj_steps_per_s_graph": ts / t_graph,
+            "traj_steps_per_s_one_by_one": ts / t_seq, "speedup": t_seq / t_graph}
 
 
 def continuation_points(fse, ctx, wl, K):
@@ -412,6 +442,9 @@ def main():
                 "traffic": recorded_traffic("k_" + kname, wl.name),
                 "peak_source": ("%s of %s (HBM copy)" % (hbm_peak, src)) if kk["bound"] == "hbm" else
                 ("152 SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (lanes, sm_mhz))}
+    batch = None
+    if args.batch:
+        batch = batch_points(fse, local)
     cont = None
     if args.points > 0:
         cont = continuation_points(fse, ctx, wl, args.points)
@@ -440,6 +473,8 @@ def main():
     }
     if cont is not None:
         line["continuation"] = cont
+    if batch is not None:
+        line["batch"] = batch
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

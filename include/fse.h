@@ -216,6 +216,33 @@ int fse_lyapunov(fse_ctx* ctx, const double* Z0, double omega1, int N_Ly, int h,
 int fse_lyapunov_noalloc(fse_ctx* ctx, const double* Z0, double omega1, int N_Ly, int h,
                          double* sigma_out);
 
+typedef struct fse_batch fse_batch;
+
+/* Several contexts evaluated together (the paper evaluates one point at a time;
+ * this runs the residual and Jacobian of Eq. 16 / Eq. 22 for a set of
+ * continuation points, possibly of different N and H, concurrently).  All
+ * contexts must be on one device and distinct; the batch does not own them
+ * (destroy the batch before its contexts).  use_graph = 0: the evaluations are
+ * enqueued back to back on the contexts' own streams and overlap on the GPU.
+ * use_graph = 1: the evaluations of all contexts (every Newmark step of their
+ * two-stream loops) are captured once into one CUDA graph on the batch's own
+ * stream and replayed by later calls with the same w_1 values and
+ * want_jacobian; a change of either re-captures it.  Per-kernel profiling of
+ * the contexts must be off in graph mode. */
+int fse_batch_create(fse_ctx* const* ctxs, int count, int use_graph, fse_batch** out);
+/* Free the batch (its stream, events and graph; not the contexts). */
+void fse_batch_destroy(fse_batch* batch);
+/* Text of the last batch error. */
+const char* fse_batch_last_error(const fse_batch* batch);
+/* Evaluate every context of the batch: Z0[i] (host, 2 n_i U~_i doubles, the
+ * layout of fse_residual_jacobian) at omega1[i] -> R_out[i] (host); the
+ * Jacobian (monodromies and the w_1 column) stays in each context as after
+ * fse_residual_jacobian with want_jacobian.  status_out (nullable, count ints)
+ * receives each context's status.  Returns FSE_OK, FSE_ENOCONV (some
+ * per-step Newton did not converge) or the first error. */
+int fse_batch_residual_jacobian(fse_batch* batch, const double* const* Z0, const double* omega1,
+                                double* const* R_out, int want_jacobian, int* status_out);
+
 /* Integrate only the first n_steps (> 0) Newmark steps of the period in the
  * following evaluations; 0 restores the full period S1.  With n_steps < S1
  * the "residual" is the DFT of the truncated trajectories' end states minus

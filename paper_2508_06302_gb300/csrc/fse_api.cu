@@ -669,7 +669,10 @@ static int collect_status(fse_ctx* c, int* ts, int* it) {
         return set_err(c, FSE_ECUDA, "a pipeline wait of the tangent kernels timed out");
     }
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) c->timing[0] = ms;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess)
+        c->timing[0] = ms;
+    else
+        cudaGetLastError();   // no timing for an evaluation replayed from a graph: clear that error
     if (c->prof_pending) {
         const int S1 = c->p.S1;
         const int steps = c->prof_steps;
@@ -1053,6 +1056,171 @@ extern "C" int fse_lyapunov_noalloc(fse_ctx* c, const double* Z0, double w, int 
     if (st < 0 && st != FSE_ENOCONV) return st;
     rc = fse::lyapunov_run_noalloc(c, w, N_Ly, h, sigma);
     return rc ? rc : st;
+}
+
+// ----------------------------------------------------------------------------
+// several contexts (continuation points, possibly of different N) evaluated together
+// ----------------------------------------------------------------------------
+
+struct fse_batch {
+    std::vector<fse_ctx*> ctx;
+    int device = 0;
+    bool use_graph = false;
+    cudaStream_t master = nullptr;   // graph mode: capture origin and launch stream
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double> w;           // w_1 of each context in the captured graph
+    int sens = -1;                   // want_jacobian of the captured graph (-1: none)
+    std::string err;
+};
+
+static void batch_free(fse_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->master) cudaStreamDestroy(b->master);
+    delete b;
+}
+
+extern "C" int fse_batch_create(fse_ctx* const* ctxs, int count, int use_graph, fse_batch** out) {
+    if (!out) return FSE_EINVAL;
+    *out = nullptr;
+    if (!ctxs || count < 1) return FSE_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) return FSE_EINVAL;
+        if (ctxs[i]->device != ctxs[0]->device) return set_err(ctxs[0], FSE_EINVAL, "batch contexts on different devices");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return set_err(ctxs[0], FSE_EINVAL, "a context appears twice in the batch");
+    }
+    fse_batch* b = new (std::nothrow) fse_batch();
+    if (!b) return FSE_ENOMEM;
+    b->ctx.assign(ctxs, ctxs + count);
+    b->device = ctxs[0]->device;
+    b->use_graph = use_graph != 0;
+    cudaSetDevice(b->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    b->join.assign(count, nullptr);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return FSE_ECUDA;
+    }
+    *out = b;
+    return FSE_OK;
+}
+
+extern "C" void fse_batch_destroy(fse_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->master) cudaStreamSynchronize(b->master);
+    batch_free(b);
+}
+
+extern "C" const char* fse_batch_last_error(const fse_batch* b) { return b ? b->err.c_str() : ""; }
+
+// capture the evaluations of all contexts at the current w_1 values into one graph
+static int batch_capture(fse_batch* b, const double* w, int sens) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->master, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        b->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        return FSE_ECUDA;
+    }
+    cudaEventRecord(b->fork, b->master);
+    int rc = FSE_OK;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        fse_ctx* c = b->ctx[i];
+        cudaStreamWaitEvent(c->stream, b->fork, 0);
+        const int r = run_eval(c, c->d.Z0, w[i], c->d.R, sens);
+        if (r && !rc) {
+            rc = r;
+            b->err = c->err;
+        }
+        cudaEventRecord(b->join[i], c->stream);
+        cudaStreamWaitEvent(b->master, b->join[i], 0);
+    }
+    e = cudaStreamEndCapture(b->master, &b->graph);
+    if (rc) return rc;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        b->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        return FSE_ECUDA;
+    }
+    b->w.assign(w, w + b->ctx.size());
+    b->sens = sens;
+    return FSE_OK;
+}
+
+extern "C" int fse_batch_residual_jacobian(fse_batch* b, const double* const* Z0, const double* omega1,
+                                           double* const* R_out, int sens, int* status_out) {
+    if (!b || !Z0 || !omega1 || !R_out) return FSE_EINVAL;
+    const int count = (int)b->ctx.size();
+    for (int i = 0; i < count; ++i) {
+        if (!Z0[i] || !R_out[i]) return FSE_EINVAL;
+        if (!(omega1[i] > 0.0) || !std::isfinite(omega1[i])) {
+            b->err = "omega1 must be positive and finite";
+            return FSE_EINVAL;
+        }
+    }
+    cudaSetDevice(b->device);
+    sens = sens ? 1 : 0;
+    if (b->use_graph) {
+        bool same = b->exec && b->sens == sens;
+        for (int i = 0; same && i < count; ++i) same = b->w[i] == omega1[i];
+        // the inputs go to the contexts' start buffers on the launch stream, before the graph
+        for (int i = 0; i < count; ++i) {
+            fse_ctx* c = b->ctx[i];
+            cudaMemcpyAsync(c->d.Z0, Z0[i], (size_t)2 * c->p.n * c->p.U * 8, cudaMemcpyHostToDevice, b->master);
+        }
+        if (!same) {
+            // the capture waits for nothing the contexts still run: drain them and the copies first
+            for (fse_ctx* c : b->ctx) cudaStreamSynchronize(c->stream);
+            cudaStreamSynchronize(b->master);
+            const int rc = batch_capture(b, omega1, sens);
+            if (rc) return rc;
+        }
+        cudaError_t e = cudaGraphLaunch(b->exec, b->master);
+        if (e != cudaSuccess) {
+            b->err = std::string("graph launch: ") + cudaGetErrorString(e);
+            return FSE_ECUDA;
+        }
+        cudaEventRecord(b->done, b->master);
+        for (fse_ctx* c : b->ctx) cudaStreamWaitEvent(c->stream, b->done, 0);
+    } else {
+        for (int i = 0; i < count; ++i) {
+            fse_ctx* c = b->ctx[i];
+            cudaMemcpyAsync(c->d.Z0, Z0[i], (size_t)2 * c->p.n * c->p.U * 8, cudaMemcpyHostToDevice, c->stream);
+            const int rc = run_eval(c, c->d.Z0, omega1[i], c->d.R, sens);
+            if (rc) {
+                b->err = c->err;
+                return rc;
+            }
+        }
+    }
+    int worst = FSE_OK;
+    for (int i = 0; i < count; ++i) {
+        fse_ctx* c = b->ctx[i];
+        cudaMemcpyAsync(R_out[i], c->d.R, (size_t)2 * c->p.n * c->p.U * 8, cudaMemcpyDeviceToHost, c->stream);
+        const int st = collect_status(c, nullptr, nullptr);
+        if (status_out) status_out[i] = st;
+        if (st < 0 && st != FSE_ENOCONV) {
+            b->err = c->err;
+            return st;
+        }
+        if (st != FSE_OK && worst == FSE_OK) worst = st;
+    }
+    return worst;
 }
 
 extern "C" int fse_set_steps(fse_ctx* c, int n_steps) {

@@ -108,6 +108,11 @@ def load(path: Optional[str] = None):
         "fse_mlp_grad": (ctypes.c_int, [_VP, _FP, _FP, ctypes.c_int, _FP, _FP]),
         "fse_mlp_train": (ctypes.c_int, [_VP, _FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_float, _FP]),
         "fse_pod_build": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP]),
+        "fse_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "fse_batch_destroy": (None, [_VP]),
+        "fse_batch_last_error": (ctypes.c_char_p, [_VP]),
+        "fse_batch_residual_jacobian": (ctypes.c_int, [_VP, ctypes.POINTER(_DP), _DP, ctypes.POINTER(_DP),
+                                                       ctypes.c_int, _IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -319,6 +324,43 @@ class Context:
 
 def _fp(a: np.ndarray):
     return a.ctypes.data_as(_FP)
+
+
+class Batch:
+    """fse_batch_*: evaluate several contexts together (own streams, or one CUDA graph)."""
+
+    def __init__(self, contexts, use_graph=False):
+        self.ctx = list(contexts)
+        arr = (_VP * len(self.ctx))(*[c.h for c in self.ctx])
+        h = _VP()
+        rc = load().fse_batch_create(arr, len(self.ctx), int(bool(use_graph)), ctypes.byref(h))
+        if rc:
+            raise FSEError(rc, fse_last_error(self.ctx[0].h))
+        self.h = h.value
+
+    def residual_jacobian(self, Z0s, omegas, want_jacobian=True):
+        """Returns (list of R, status array, rc)."""
+        Zs = [np.ascontiguousarray(z, dtype=np.float64) for z in Z0s]
+        Rs = [np.zeros(c.n_unknowns) for c in self.ctx]
+        zp = (_DP * len(Zs))(*[_dp(z) for z in Zs])
+        rp = (_DP * len(Rs))(*[_dp(r) for r in Rs])
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        st = np.zeros(len(self.ctx), np.int32)
+        rc = load().fse_batch_residual_jacobian(self.h, zp, _dp(om), rp, int(bool(want_jacobian)), _ip(st))
+        if rc not in (FSE_OK, FSE_ENOCONV):
+            raise FSEError(rc, load().fse_batch_last_error(self.h).decode())
+        return Rs, st, rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fse_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mlp:
