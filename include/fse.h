@@ -152,6 +152,11 @@ int fse_jacobian_dense(fse_ctx* ctx, double* J);
  * d zbar_s(2 pi)/d w_1 (N x 2n) of the last evaluation (either may be NULL). */
 int fse_monodromy(fse_ctx* ctx, double* Phi, double* dz_dw);
 
+/* The monodromy block Phi_s (2n x 2n, row-major) and d zbar_s(2 pi)/d w_1 (2n)
+ * of trajectory s of the last evaluation (either may be NULL): one block of
+ * fse_monodromy without copying all N.  FSE_EINVAL for s outside [0, N). */
+int fse_monodromy_traj(fse_ctx* ctx, int s, double* Phi, double* dz_dw);
+
 /* One Newton-Raphson update of Z(0) at fixed w_1 (Sec. 3.3 step 6): evaluates
  * R and J at Z0, solves J dZ = -R on the GPU with the solver chosen by
  * fse_set_linear_solver (dense LU up to 16384 unknowns, matrix-free GMRES

@@ -348,6 +348,18 @@ void launch_phi_copy(fse_ctx* c, double* Phi, double* dzdw) {
                                                                  (const double*)c->d.V, Phi, dzdw);
 }
 
+void launch_phi_copy_one(fse_ctx* c, int s, double* Phi, double* dzdw) {
+    const Params& p = c->p;
+    const size_t tot = (size_t)4 * p.n * p.n;
+    const size_t off = (size_t)s * p.n * p.ld;
+    if (p.prec == FSE_MIXED_FP32)
+        k_phi_copy<float><<<nblocks(tot, 256), 256, 0, c->stream>>>(1, p.n, p.ld, (const float*)c->d.X + off,
+                                                                (const float*)c->d.V + off, Phi, dzdw);
+    else
+        k_phi_copy<double><<<nblocks(tot, 256), 256, 0, c->stream>>>(1, p.n, p.ld, (const double*)c->d.X + off,
+                                                                 (const double*)c->d.V + off, Phi, dzdw);
+}
+
 void launch_dense_jac(fse_ctx* c, double* J) {
     const Params& p = c->p;
     const size_t m = (size_t)2 * p.n * p.U;

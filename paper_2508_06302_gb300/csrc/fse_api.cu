@@ -810,6 +810,28 @@ extern "C" int fse_monodromy(fse_ctx* c, double* Phi, double* dzdw) {
     return rc;
 }
 
+extern "C" int fse_monodromy_traj(fse_ctx* c, int s, double* Phi, double* dzdw) {
+    if (!c) return FSE_EINVAL;
+    if (s < 0 || s >= c->p.N) return set_err(c, FSE_EINVAL, "trajectory index out of range");
+    if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored");
+    cudaSetDevice(c->device);
+    const size_t n2 = 2 * (size_t)c->p.n;
+    double *dP = nullptr, *dz = nullptr;
+    cudaError_t e = cudaMalloc(&dP, n2 * n2 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dz, n2 * 8);
+    if (e != cudaSuccess) {
+        if (dP) cudaFree(dP);
+        return cuda_check(c, e, "monodromy buffer");
+    }
+    fse::launch_phi_copy_one(c, s, dP, dz);
+    if (Phi) cudaMemcpyAsync(Phi, dP, n2 * n2 * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (dzdw) cudaMemcpyAsync(dzdw, dz, n2 * 8, cudaMemcpyDeviceToHost, c->stream);
+    int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "monodromy");
+    cudaFree(dP);
+    cudaFree(dz);
+    return rc;
+}
+
 // ||R||_2 and ||Z(0)||_2 of the last evaluation (device reduction, two scalars back)
 static int norms_RZ(fse_ctx* c, double* rn, double* zn) {
     const size_t m = (size_t)2 * c->p.n * c->p.U;

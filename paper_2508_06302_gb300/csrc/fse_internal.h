@@ -195,6 +195,7 @@ void launch_dft_residual(fse_ctx* c, const double* zb, const double* Z0, double*
 void launch_phi_apply(fse_ctx* c, const double* zin, double* zout);
 void launch_domega(fse_ctx* c, double* zout);
 void launch_phi_copy(fse_ctx* c, double* Phi_dev, double* dzdw_dev);
+void launch_phi_copy_one(fse_ctx* c, int s, double* Phi_dev, double* dzdw_dev);
 void launch_dense_jac(fse_ctx* c, double* J);
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);

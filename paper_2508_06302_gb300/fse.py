@@ -89,6 +89,7 @@ def load(path: Optional[str] = None):
         "fse_jacobian_domega": (ctypes.c_int, [_VP, _DP]),
         "fse_jacobian_dense": (ctypes.c_int, [_VP, _DP]),
         "fse_monodromy": (ctypes.c_int, [_VP, _DP, _DP]),
+        "fse_monodromy_traj": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
         "fse_newton_step": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP]),
         "fse_lyapunov": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
         "fse_lyapunov_noalloc": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
@@ -273,6 +274,13 @@ class Context:
         Phi = np.zeros((self.N, 2 * self.n, 2 * self.n))
         dz = np.zeros((self.N, 2 * self.n))
         self._check(load().fse_monodromy(self.h, _dp(Phi), _dp(dz)))
+        return Phi, dz
+
+    def monodromy_traj(self, s):
+        """fse_monodromy_traj: (Phi_s, d zbar_s / d w_1) of trajectory s."""
+        Phi = np.zeros((2 * self.n, 2 * self.n))
+        dz = np.zeros(2 * self.n)
+        self._check(load().fse_monodromy_traj(self.h, int(s), _dp(Phi), _dp(dz)))
         return Phi, dz
 
     def newton_step(self, Z0, omega1):
