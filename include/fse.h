@@ -324,12 +324,15 @@ int fse_pod_build(const double* snaps, int nu, int m, int r, double* mean, doubl
  * One-parameter continuation in w_1 (App. C, natural parameter with the
  * frequency ratios fixed, Eq. Cont2).  Point j is predicted, then corrected by
  * Newton on Eq. (16) at fixed w_1 until ||R||_2 <= rel_tol ||Z(0)||_2.
- * Predictors: the secant through the last two accepted points, or the network
- * (after `warmup` points): Z = mean + sum_k c_k mode_k with c from the MLP fed
- * (w_1, w_2, F_1) normalised to [-1, 1] over [omega_lo, omega_hi]; the POD is
- * rebuilt every pod_every points from all accepted points and the network is
- * trained on their coefficients (each mode divided by its RMS over the
- * accepted points, the scale the prediction multiplies back) for train_steps
+ * Predictors: the secant S_j through the last two accepted points, or the
+ * secant corrected by the network (from point max(4, warmup) on):
+ * Z = S_j + mean + sum_k c_k mode_k, c from the MLP fed (w_1, w_2, F_1)
+ * normalised to [-1, 1] over [omega_lo, omega_hi].  The network learns the
+ * secant's own error: after every accepted point j >= 2 the correction
+ * Z_j - S_j is stored, the POD of the corrections is rebuilt every pod_every
+ * points and the network is trained on their coefficients (each mode divided
+ * by its RMS over the corrections, the scale the prediction multiplies back;
+ * modes below 1e-8 of the first are not learned) for train_steps
  * Adam steps after every point.  The outer linear solve is the one of
  * fse_newton_step (fse_set_linear_solver).
  * ------------------------------------------------------------------------ */

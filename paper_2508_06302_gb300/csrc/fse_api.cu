@@ -1285,13 +1285,15 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
     const int P = o->n_points;
     if (o->predictor == FSE_PRED_MLP && (o->pod_modes < 1 || fse_mlp_nouts(mlp) != o->pod_modes))
         return set_err(c, FSE_EINVAL, "network outputs must equal pod_modes");
-    double *Zs = nullptr, *Zp = nullptr, *Sscr = nullptr, *pmean = nullptr, *pbasis = nullptr, *coef = nullptr,
-           *cdev = nullptr;
+    double *Zs = nullptr, *Zp = nullptr, *Sec = nullptr, *Dsn = nullptr, *Sscr = nullptr, *pmean = nullptr,
+           *pbasis = nullptr, *coef = nullptr, *cdev = nullptr;
     cudaError_t e = cudaMalloc(&Zs, (size_t)P * nu * 8);
     if (e == cudaSuccess) e = cudaMalloc(&Zp, nu * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&Sec, nu * 8);
     const bool learn = o->predictor == FSE_PRED_MLP;
     const int rmax = std::max(1, o->pod_modes);
     if (learn) {
+        if (e == cudaSuccess) e = cudaMalloc(&Dsn, (size_t)P * nu * 8);   // corrections Z_a - S_a, a >= 2
         if (e == cudaSuccess) e = cudaMalloc(&Sscr, (size_t)P * nu * 8);
         if (e == cudaSuccess) e = cudaMalloc(&pmean, nu * 8);
         if (e == cudaSuccess) e = cudaMalloc(&pbasis, (size_t)rmax * nu * 8);
@@ -1299,7 +1301,8 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
         if (e == cudaSuccess) e = cudaMalloc(&cdev, (size_t)rmax * 8);
     }
     auto cleanup = [&]() {
-        for (void* q : {(void*)Zs, (void*)Zp, (void*)Sscr, (void*)pmean, (void*)pbasis, (void*)coef, (void*)cdev})
+        for (void* q : {(void*)Zs, (void*)Zp, (void*)Sec, (void*)Dsn, (void*)Sscr, (void*)pmean, (void*)pbasis,
+                        (void*)coef, (void*)cdev})
             if (q) cudaFree(q);
     };
     if (e != cudaSuccess) {
@@ -1307,7 +1310,7 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
         return cuda_check(c, e, "continuation buffers");
     }
     int r = 0;                                 // current POD rank (0 = no basis yet)
-    int reff = 0;                              // modes above the relative threshold 1e-10
+    int reff = 0;                              // modes above the relative threshold 1e-8
     double tmax = 0.0;                         // clamp of the scaled network outputs
     std::vector<double> sing(rmax, 0.0);
     std::vector<double> tsc(rmax, 1.0);        // per-mode scale: RMS of the training coefficients
@@ -1318,37 +1321,47 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
         x[1] = (float)t;                        // w_2 = rho w_1: same normalised value
         x[2] = 0.0f;                            // F_1 fixed over the sweep
     };
+    // secant prediction S_j = (1 + q) Z_{j-1} - q Z_{j-2} into Sec (j >= 2), or Z_0 (j == 1)
+    auto secant = [&](int j) {
+        if (j == 1) {
+            cudaMemcpyAsync(Sec, Zs, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+            return;
+        }
+        const double q = (o->omega1[j] - o->omega1[j - 1]) / (o->omega1[j - 1] - o->omega1[j - 2]);
+        cudaMemcpyAsync(Sec, Zs + (size_t)(j - 1) * nu, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+        fse::vec_axpby(c, nu, -q, Zs + (size_t)(j - 2) * nu, 1.0 + q, Sec);
+    };
     int worst = FSE_OK;
     for (int j = 0; j < P; ++j) {
         const double w = o->omega1[j];
         cudaEventRecord(c->ev[4], c->stream);
-        // ---- predictor
+        // ---- predictor: secant, plus the network's correction once it has seen enough points
         bool used_mlp = false;
         if (j == 0) {
             cudaMemcpyAsync(c->d.Z0, Z_start, nu * 8, cudaMemcpyHostToDevice, c->stream);
-        } else if (learn && reff > 0 && j >= std::max(2, o->warmup)) {
-            float x[3];
-            feats(w, x);
-            std::vector<float> yy((size_t)rmax);
-            int rc = fse_mlp_forward(mlp, x, 1, yy.data());
-            if (rc) {
-                cleanup();
-                return set_err(c, rc, "network forward failed");
-            }
-            std::vector<double> cc(r, 0.0);
-            for (int k = 0; k < reff; ++k) {
-                const double t = std::max(-tmax, std::min(tmax, (double)yy[k]));
-                cc[k] = t * tsc[k];
-            }
-            cudaMemcpyAsync(cdev, cc.data(), r * 8, cudaMemcpyHostToDevice, c->stream);
-            fse::pod_expand(c, nu, r, pmean, pbasis, cdev, c->d.Z0);
-            used_mlp = true;
-        } else if (j == 1) {
-            cudaMemcpyAsync(c->d.Z0, Zs, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
         } else {
-            const double q = (w - o->omega1[j - 1]) / (o->omega1[j - 1] - o->omega1[j - 2]);
-            cudaMemcpyAsync(c->d.Z0, Zs + (size_t)(j - 1) * nu, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
-            fse::vec_axpby(c, nu, -q, Zs + (size_t)(j - 2) * nu, 1.0 + q, c->d.Z0);   // (1+q) Z_{j-1} - q Z_{j-2}
+            secant(j);
+            if (learn && reff > 0 && j >= std::max(4, o->warmup)) {
+                float x[3];
+                feats(w, x);
+                std::vector<float> yy((size_t)rmax);
+                int rc = fse_mlp_forward(mlp, x, 1, yy.data());
+                if (rc) {
+                    cleanup();
+                    return set_err(c, rc, "network forward failed");
+                }
+                std::vector<double> cc(r, 0.0);
+                for (int k = 0; k < reff; ++k) {
+                    const double t = std::max(-tmax, std::min(tmax, (double)yy[k]));
+                    cc[k] = t * tsc[k];
+                }
+                cudaMemcpyAsync(cdev, cc.data(), r * 8, cudaMemcpyHostToDevice, c->stream);
+                fse::pod_expand(c, nu, r, pmean, pbasis, cdev, c->d.Z0);   // predicted correction
+                fse::vec_axpby(c, nu, 1.0, Sec, 1.0, c->d.Z0);             // + secant
+                used_mlp = true;
+            } else {
+                cudaMemcpyAsync(c->d.Z0, Sec, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+            }
         }
         cudaMemcpyAsync(Zp, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
         // ---- corrector: Newton on Eq. (16) at fixed w_1, accepted when ||R|| <= tol ||Z||
@@ -1356,10 +1369,8 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
         int it = 0, evals = 1;
         int st = eval_at_iterate(c, w, 1, &rn, &zn);
         if (used_mlp && (st < FSE_ENOCONV || !std::isfinite(rn))) {
-            // the network prediction left the basin: fall back to the secant prediction
-            const double q = (w - o->omega1[j - 1]) / (o->omega1[j - 1] - o->omega1[j - 2]);
-            cudaMemcpyAsync(c->d.Z0, Zs + (size_t)(j - 1) * nu, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
-            fse::vec_axpby(c, nu, -q, Zs + (size_t)(j - 2) * nu, 1.0 + q, c->d.Z0);
+            // the corrected prediction left the basin: fall back to the secant prediction
+            cudaMemcpyAsync(c->d.Z0, Sec, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
             cudaMemcpyAsync(Zp, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
             used_mlp = false;
             st = eval_at_iterate(c, w, 1, &rn, &zn);
@@ -1406,53 +1417,59 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
             info[j].status = pst;
             info[j].predictor = used_mlp ? FSE_PRED_MLP : FSE_PRED_SECANT;
         }
-        // ---- learning: POD of the accepted tori, network trained on their coefficients
-        if (learn && j >= 1) {
-            const int m = j + 1;
-            const bool rebuild = (m % std::max(1, o->pod_every) == 0) || r == 0;
-            if (rebuild) {
-                const int rr = std::min(rmax, m - 1);
-                cudaMemcpyAsync(Sscr, Zs, (size_t)m * nu * 8, cudaMemcpyDeviceToDevice, c->stream);
-                rc = fse::pod_build_dev(Sscr, (int)nu, m, rr, pmean, pbasis, sing.data(), c->stream);
+        // ---- learning: the secant's correction Z_j - S_j of every accepted point j >= 2, its
+        // POD, and the network trained on the scaled coefficients
+        if (learn && j >= 2) {
+            double* dj = Dsn + (size_t)(j - 2) * nu;
+            cudaMemcpyAsync(dj, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+            fse::vec_axpby(c, nu, -1.0, Sec, 1.0, dj);
+            const int m = j - 1;   // corrections known
+            if (m >= 2) {
+                const bool rebuild = (m % std::max(1, o->pod_every) == 0) || r == 0;
+                if (rebuild) {
+                    const int rr = std::min(rmax, m - 1);
+                    cudaMemcpyAsync(Sscr, Dsn, (size_t)m * nu * 8, cudaMemcpyDeviceToDevice, c->stream);
+                    rc = fse::pod_build_dev(Sscr, (int)nu, m, rr, pmean, pbasis, sing.data(), c->stream);
+                    if (rc) {
+                        cleanup();
+                        return set_err(c, rc, "POD build failed");
+                    }
+                    r = rr;
+                    reff = 0;
+                    while (reff < r && sing[reff] > 1e-8 * sing[0]) ++reff;
+                }
+                fse::pod_project(c, nu, r, m, pmean, pbasis, Dsn, coef);
+                std::vector<double> ch((size_t)m * r);
+                cudaMemcpyAsync(ch.data(), coef, ch.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+                rc = cuda_check(c, cudaStreamSynchronize(c->stream), "POD projection");
                 if (rc) {
                     cleanup();
-                    return set_err(c, rc, "POD build failed");
+                    return rc;
                 }
-                r = rr;
-                reff = 0;
-                while (reff < r && sing[reff] > 1e-10 * sing[0]) ++reff;
-            }
-            fse::pod_project(c, nu, r, m, pmean, pbasis, Zs, coef);
-            std::vector<double> ch((size_t)m * r);
-            cudaMemcpyAsync(ch.data(), coef, ch.size() * 8, cudaMemcpyDeviceToHost, c->stream);
-            rc = cuda_check(c, cudaStreamSynchronize(c->stream), "POD projection");
-            if (rc) {
-                cleanup();
-                return rc;
-            }
-            const int no = o->pod_modes;
-            std::vector<float> X((size_t)m * 3), T((size_t)m * no, 0.0f);
-            // targets: coefficients divided by their RMS over the training set, mode by mode
-            // (modes below the rank threshold are not learned)
-            tmax = 0.0;
-            for (int k = 0; k < reff; ++k) {
-                double s2 = 0.0;
-                for (int a = 0; a < m; ++a) s2 += ch[(size_t)a * r + k] * ch[(size_t)a * r + k];
-                tsc[k] = std::max(std::sqrt(s2 / m), 1e-300);
-            }
-            for (int a = 0; a < m; ++a) {
-                feats(o->omega1[a], &X[(size_t)a * 3]);
+                const int no = o->pod_modes;
+                std::vector<float> X((size_t)m * 3), T((size_t)m * no, 0.0f);
+                // targets: coefficients divided by their RMS over the training set, mode by mode
+                // (modes below the rank threshold are not learned)
+                tmax = 0.0;
                 for (int k = 0; k < reff; ++k) {
-                    const double t = ch[(size_t)a * r + k] / tsc[k];
-                    T[(size_t)a * no + k] = (float)t;
-                    tmax = std::max(tmax, 2.0 * std::fabs(t));
+                    double s2 = 0.0;
+                    for (int a = 0; a < m; ++a) s2 += ch[(size_t)a * r + k] * ch[(size_t)a * r + k];
+                    tsc[k] = std::max(std::sqrt(s2 / m), 1e-300);
                 }
-            }
-            float loss = 0.f;
-            rc = fse_mlp_train(mlp, X.data(), T.data(), m, o->train_steps, o->lr, &loss);
-            if (rc) {
-                cleanup();
-                return set_err(c, rc, "network training failed");
+                for (int a = 0; a < m; ++a) {
+                    feats(o->omega1[a + 2], &X[(size_t)a * 3]);
+                    for (int k = 0; k < reff; ++k) {
+                        const double t = ch[(size_t)a * r + k] / tsc[k];
+                        T[(size_t)a * no + k] = (float)t;
+                        tmax = std::max(tmax, 2.0 * std::fabs(t));
+                    }
+                }
+                float loss = 0.f;
+                rc = fse_mlp_train(mlp, X.data(), T.data(), m, o->train_steps, o->lr, &loss);
+                if (rc) {
+                    cleanup();
+                    return set_err(c, rc, "network training failed");
+                }
             }
         }
     }
