@@ -47,6 +47,8 @@ def parse():
                     help="small case: integrate only the first K Newmark steps of the period")
     ap.add_argument("--batch", action="store_true",
                     help="also time the 8-point shell batch (N = 32..64) as one graph against one by one")
+    ap.add_argument("--predictor", default="secant", choices=["secant", "mlp", "both"],
+                    help="continuation predictor of --points (both: the two sweeps one after the other)")
     ap.add_argument("--points", type=int, default=0,
                     help="also time K converged continuation points (secant predictor, chord corrector)")
     return ap.parse_args()
@@ -253,24 +255,36 @@ def batch_points(fse, device):
             "traj_steps_per_s_one_by_one": ts / t_seq, "speedup": t_seq / t_graph}
 
 
-def continuation_points(fse, ctx, wl, K):
+def continuation_points(fse, ctx, wl, K, predictor="secant", device=0):
     """K + 1 points of the w_1 sweep from 0.90 w_n1 in steps of 0.002 w_n1: the first converged
-    from the discrete linear response (not counted), then K points with the secant predictor and
-    the chord corrector (one Jacobian per point, GMRES on the structured products for the outer
-    solve), each accepted at ||R|| <= 1e-10 ||Z|| (FP64 residual)."""
+    from the discrete linear response (not counted), then K points with the secant predictor, or
+    the secant corrected by the BF16 network trained online on the secant's errors (64 POD modes,
+    warm-up 4 points), and the chord corrector (one Jacobian per point, GMRES on the structured
+    products for the outer solve), each accepted at ||R|| <= 1e-10 ||Z|| (FP64 residual)."""
     import dataclasses
+    from paper_2508_06302_gb300 import inputs as I
     w_n1 = wl.model.omega_n1
     omegas = w_n1 * (0.90 + 0.002 * np.arange(K + 1))
     Z0 = initial_coeffs(dataclasses.replace(wl, omega1=float(omegas[0])))
     ctx.set_steps(0)
     ctx.profile(False)
-    Z, pts, rc = fse.fse_continue(ctx, omegas, Z0, rel_tol=1e-10, max_newton=40, chord=True)
+    net = None
+    kw = {}
+    if predictor == "mlp":
+        net = fse.Mlp(3, 256, 64, max_batch=max(64, K + 1), device=device)
+        net.set_params(I.mlp_init(3, 256, 64, seed=0))
+        kw = dict(predictor="mlp", mlp=net, warmup=4, pod_modes=64, pod_every=1, train_steps=300, lr=2e-3)
+    Z, pts, rc = fse.fse_continue(ctx, omegas, Z0, rel_tol=1e-10, max_newton=40, chord=True, **kw)
+    if net is not None:
+        net.close()
     timed = pts[1:]
     tot_ms = sum(p["ms"] for p in timed)
     lin = ctx.linear_stats()
-    return {"points": K, "points_per_s": K / (tot_ms / 1e3) if tot_ms > 0 else None,
+    return {"points": K, "predictor": predictor, "points_per_s": K / (tot_ms / 1e3) if tot_ms > 0 else None,
             "ms_per_point": [round(p["ms"], 1) for p in timed],
             "newton_iters": [p["newton_iters"] for p in timed],
+            "pred_err": [p["pred_err"] for p in timed],
+            "learned_used": [p["predictor"] == fse.FSE_PRED_MLP for p in timed],
             "jacobian_evals_per_point": 1,
             "residual_evals": [p["evals"] - 1 for p in timed],
             "rel_res": [p["res"] / p["znorm"] for p in timed],
@@ -447,7 +461,8 @@ def main():
         batch = batch_points(fse, local)
     cont = None
     if args.points > 0:
-        cont = continuation_points(fse, ctx, wl, args.points)
+        cont = {p: continuation_points(fse, ctx, wl, args.points, p, local)
+                for p in (["secant", "mlp"] if args.predictor == "both" else [args.predictor])}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, args.cpu_seconds)
