@@ -143,6 +143,28 @@ class Clocks:
         return out
 
 
+def rank_omega(wl, rank):
+    """Every rank solves its own continuation point (weak scaling, no exchange of
+    trajectory data): w_1 of rank r is the workload's w_1 times 1 + 0.01 r."""
+    return wl.omega1 * (1.0 + 0.01 * rank)
+
+
+def max_over_ranks(ms, world, device):
+    """Step time of the whole job: the slowest rank's (all-reduce MAX; the only collective)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -343,7 +365,7 @@ def main():
                                  name=wl.name + "_N%d" % args.traj)
     m = wl.model
     # every rank runs its own continuation point (weak scaling, no exchange)
-    w1 = wl.omega1 * (1.0 + 0.01 * rank)
+    w1 = rank_omega(wl, rank)
     ctx = fse.Context.from_workload(wl, precision=args.precision, device=local)
     ctx.profile(True)
     n_newmark = wl.S1
@@ -380,12 +402,10 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, world, "cuda")
         torch.distributed.barrier()
     traj_steps = wl.N * n_newmark
-    value = traj_steps * world / (ms / 1e3)
+    value = job_value(traj_steps, world, ms)
     phase /= args.steps                 # per step; phase[5] is the mean refactor count
 
     # end-to-end through the host-pointer API (H2D of Z(0), D2H of R inside the timed region)
