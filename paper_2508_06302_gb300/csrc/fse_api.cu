@@ -630,7 +630,7 @@ static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, i
     for (int k = 0; k < steps; ++k) {
         if (sens && k >= 2) cudaStreamWaitEvent(s1, c->ev_sens[k - 2], 0);
         rec(0, k, 0, s1);
-        fse::launch_state_step(c, k, w, s1);
+        fse::launch_state_step(c, k, w, s1, sens != 0);
         rec(0, k, 1, s1);
         if (sens) {
             cudaEventRecord(c->ev_state[k], s1);

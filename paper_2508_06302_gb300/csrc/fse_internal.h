@@ -187,7 +187,7 @@ void launch_build_groups(fse_ctx* c);
 int launch_factor_M(fse_ctx* c);
 void launch_idft(fse_ctx* c, const double* Z, double* zb);
 void launch_init_state(fse_ctx* c, double omega1);
-void launch_state_step(fse_ctx* c, int k, double omega1, cudaStream_t st);
+void launch_state_step(fse_ctx* c, int k, double omega1, cudaStream_t st, bool sens);
 void launch_sens_init(fse_ctx* c, cudaStream_t st);
 void launch_sens_phase(fse_ctx* c, int k, double omega1, int phase, cudaStream_t st);
 void launch_collect_end(fse_ctx* c);

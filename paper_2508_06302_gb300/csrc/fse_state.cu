@@ -346,6 +346,7 @@ __device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int 
 
 struct StateArgs {
     int n, b, e, dm1, maxit, ncolors, n_el, nnz_kt, kt_ld, nblk, init;
+    int refactor;       // 0: keep the previous factors (residual-only steps, see launch_state_step)
     double tol, Dl, a0c, a1c, a2c, w, phi;
     double rho[FSE_MAX_D - 1];
     const double *F, *phis;
@@ -725,9 +726,12 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         __syncthreads();
     }
     // effective stiffness at the new state, its banded Cholesky factor and block inverses
-    assemble_keff<T>(A, s, sq, oLc, kt_out);
-    const int bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE);
-    if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
+    int bad = 0;
+    if (A.refactor) {
+        assemble_keff<T>(A, s, sq, oLc, kt_out);
+        bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE);
+        if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
+    }
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
         A.status[s] = s_stat;
@@ -901,14 +905,21 @@ void launch_init_state(fse_ctx* c, double w) {
     const size_t tot = (size_t)p.N * p.n;
     k_split<<<nblocks(tot, 256), 256, 0, c->stream>>>(p.N, p.n, c->d.zb, c->d.q, c->d.u);
     StateArgs A = make_state_args(c, w, 1, -1);
+    A.refactor = 1;
     if (p.prec == FSE_MIXED_FP32)
         state_launch<float>(c, A, c->stream);
     else
         state_launch<double>(c, A, c->stream);
 }
 
-void launch_state_step(fse_ctx* c, int k, double w, cudaStream_t st) {
+// Without tangents (residual-only evaluations) the factor at the end of a step only serves as
+// the chord matrix of the next step's Newton, whose FP64 residual makes any recent factor
+// good enough; those evaluations refactor on two consecutive steps out of four (both parity
+// buffers stay at most four steps old) and always on steps 0 and 1, and the in-loop refactor
+// of k_state still reacts to a slow contraction.
+void launch_state_step(fse_ctx* c, int k, double w, cudaStream_t st, bool sens) {
     StateArgs A = make_state_args(c, w, 0, k);
+    A.refactor = (sens || k < 2 || (k & 3) < 2) ? 1 : 0;
     if (c->p.prec == FSE_MIXED_FP32)
         state_launch<float>(c, A, st);
     else
