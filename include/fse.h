@@ -373,6 +373,42 @@ typedef struct {
 int fse_continue(fse_ctx* ctx, fse_mlp* mlp, const fse_cont_opts* opts, const double* Z_start,
                  double* Z_out, fse_cont_point* info);
 
+/* ------------------------------------------------------------------------
+ * Pseudo-arclength continuation in (Z(0), w_1) (App. C, Eq. C1-C3), which
+ * follows the branch through folds where stepping w_1 fails.  Point 0 is
+ * Z_start corrected by Newton at fixed w_1 = omega_start.  The first tangent
+ * solves [J dR/dw_1; 0 1] (t_Z, t_w) = (0, 1), oriented so that t_w has the
+ * sign of `direction`; later tangents are the secant through the last two
+ * points.  Distances use ||dZ||^2 + (sigma dw_1)^2, sigma = omega_scale (<= 0:
+ * ||Z_0|| / omega_start).  The step grows by 1.5 (up to ds_max) after a
+ * correction of at most 2 Newton updates, shrinks by 0.7 after one of 5 or more,
+ * and is halved (down to ds / 64) and the point predicted again when the
+ * correction fails.  Point j: predictor y_pred = y_{j-1} + ds t, then
+ * Newton on R(Z, w_1) = 0 and t . (y - y_pred) = 0 with the bordered matrix
+ * [J dR/dw_1; t_Z^T sigma^2 t_w] (Eq. 22, Eq. 23; dense LU on the GPU, so
+ * 2 n U~ <= 16383), accepted when ||R||_2 <= rel_tol ||Z||_2.  Stops after
+ * n_points, at the first point that does not converge (returns FSE_ENOCONV)
+ * or once w_1 leaves [omega_min, omega_max] (omega_max <= 0: no upper bound).
+ * Z_out: n_points x 2 n U~ doubles (host, nullable); omega_out: n_points
+ * doubles (host, nullable); info: n_points records (pred_err unused);
+ * n_done: points written.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int n_points;
+    double omega_start;        /* w_1 of Z_start                                */
+    double ds;                 /* first arclength step (> 0), metric above      */
+    double ds_max;             /* largest step (<= ds: fixed steps)             */
+    double omega_scale;        /* sigma; <= 0 for ||Z_0|| / omega_start          */
+    int direction;             /* +1: start towards larger w_1, -1: smaller     */
+    double rel_tol;            /* acceptance ||R|| <= rel_tol ||Z||             */
+    int max_newton;            /* corrector iterations per point (>= 1)         */
+    double omega_min, omega_max;
+} fse_arc_opts;
+
+/* Run the pseudo-arclength continuation described above. */
+int fse_continue_arclength(fse_ctx* ctx, const fse_arc_opts* opts, const double* Z_start, double* Z_out,
+                           double* omega_out, fse_cont_point* info, int* n_done);
+
 #ifdef __cplusplus
 }
 #endif

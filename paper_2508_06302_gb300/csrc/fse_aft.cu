@@ -98,7 +98,7 @@ __global__ void k_phi_copy(int N, int n, int P, const T* X, const T* V, double* 
 // dense Eq. (22): J[(i,u),(j,v)] = sum_s RG[u][s] Phi_s[i][j] G[s][v] - delta
 template <typename T>
 __global__ void k_dense_jac(int N, int n, int U, int P, const T* X, const T* V,
-                            const double* RG, const double* G, double* J) {
+                            const double* RG, const double* G, double* J, size_t lda) {
     const int n2 = 2 * n;
     const size_t m = (size_t)n2 * U;
     const size_t total = m * m;
@@ -112,7 +112,20 @@ __global__ void k_dense_jac(int N, int n, int U, int P, const T* X, const T* V,
             const T* xr = (i < n ? X + ((size_t)s * n + i) * P : V + ((size_t)s * n + (i - n)) * P);
             acc += RG[(size_t)uu * N + s] * (double)xr[j] * G[(size_t)s * U + vv];
         }
-        J[idx] = acc - (row == col ? 1.0 : 0.0);
+        J[row * lda + col] = acc - (row == col ? 1.0 : 0.0);
+    }
+}
+
+// border of the pseudo-arclength system: column m = dR/dw_1, row m = (t_Z, tail)
+__global__ void k_border(size_t m, const double* __restrict__ Rw, const double* __restrict__ tZ, double tail,
+                         double* B) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i <= m; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < m) {
+            B[i * (m + 1) + m] = Rw[i];
+            B[m * (m + 1) + i] = tZ[i];
+        } else {
+            B[m * (m + 1) + m] = tail;
+        }
     }
 }
 
@@ -365,10 +378,22 @@ void launch_dense_jac(fse_ctx* c, double* J) {
     const size_t m = (size_t)2 * p.n * p.U;
     if (p.prec == FSE_MIXED_FP32)
         k_dense_jac<float><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
-            p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, J);
+            p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, J, m);
     else
         k_dense_jac<double><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
-            p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, J);
+            p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, J, m);
+}
+
+void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double tail, double* B) {
+    const Params& p = c->p;
+    const size_t m = (size_t)2 * p.n * p.U;
+    if (p.prec == FSE_MIXED_FP32)
+        k_dense_jac<float><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, B, m + 1);
+    else
+        k_dense_jac<double><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, B, m + 1);
+    k_border<<<nblocks(m + 1, 256), 256, 0, c->stream>>>(m, Rw, tZ, tail, B);
 }
 
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m) {

@@ -1245,6 +1245,195 @@ extern "C" int fse_batch_residual_jacobian(fse_batch* b, const double* const* Z0
     return worst;
 }
 
+// ----------------------------------------------------------------------------
+// pseudo-arclength continuation in (Z(0), w_1) (App. C, Eq. C1-C3)
+// ----------------------------------------------------------------------------
+
+extern "C" int fse_continue_arclength(fse_ctx* c, const fse_arc_opts* o, const double* Z_start, double* Z_out,
+                                      double* omega_out, fse_cont_point* info, int* n_done) {
+    if (!c || !o || !Z_start || o->n_points < 1) return FSE_EINVAL;
+    if (n_done) *n_done = 0;
+    if (!(o->rel_tol > 0.0) || o->max_newton < 1 || !(o->ds > 0.0) || !(o->omega_start > 0.0))
+        return set_err(c, FSE_EINVAL, "need rel_tol > 0, max_newton >= 1, ds > 0, omega_start > 0");
+    cudaSetDevice(c->device);
+    const size_t m = (size_t)2 * c->p.n * c->p.U;
+    if (m + 1 > 16384) return set_err(c, FSE_EINVAL, "pseudo-arclength: bordered dense solve limited to 16383 unknowns");
+    int rc = ensure_dense(c, m + 1);
+    if (rc) return rc;
+    double *Zprev = nullptr, *Zpred = nullptr, *tZ = nullptr, *tmp = nullptr, *rhs = nullptr, *dd = nullptr;
+    cudaError_t e = cudaMalloc(&Zprev, m * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&Zpred, m * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&tZ, m * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, m * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&rhs, (m + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dd, 16);
+    auto cleanup = [&]() {
+        for (void* q : {(void*)Zprev, (void*)Zpred, (void*)tZ, (void*)tmp, (void*)rhs, (void*)dd})
+            if (q) cudaFree(q);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_check(c, e, "arclength buffers");
+    }
+    auto sq_norm = [&](const double* v) -> double {   // ||v||^2 (m entries)
+        fse::vec_norms2(c, m, v, nullptr, dd);
+        double h[2];
+        cudaMemcpyAsync(h, dd, 16, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        return h[0];
+    };
+    auto dot = [&](const double* a, const double* b) -> double {
+        fse::vec_mdot(c, m, 1, a, b, dd);
+        double h = 0.0;
+        cudaMemcpyAsync(&h, dd, 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        return h;
+    };
+    auto get_last = [&]() -> double {
+        double h = 0.0;
+        cudaMemcpyAsync(&h, rhs + m, 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        return h;
+    };
+    auto set_last = [&](double v) { cudaMemcpy(rhs + m, &v, 8, cudaMemcpyHostToDevice); };
+    auto dRdw = [&]() {   // dR/dw_1 of the last Jacobian evaluation -> d.vec2 (Eq. 23)
+        fse::launch_domega(c, c->d.yb);
+        fse::launch_dft_residual(c, c->d.yb, nullptr, c->d.vec2, 0);
+    };
+    auto record = [&](int j, double w, int it, int evals, double rn, double zn, int pst) {
+        if (Z_out) cudaMemcpyAsync(Z_out + (size_t)j * m, c->d.Z0, m * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaEventRecord(c->ev[5], c->stream);
+        cudaStreamSynchronize(c->stream);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+        if (omega_out) omega_out[j] = w;
+        if (info) {
+            info[j].newton_iters = it;
+            info[j].evals = evals;
+            info[j].res = rn;
+            info[j].znorm = zn;
+            info[j].pred_err = 0.0;
+            info[j].ms = ms;
+            info[j].status = pst;
+            info[j].predictor = FSE_PRED_SECANT;
+        }
+        if (n_done) *n_done = j + 1;
+    };
+    // ---- point 0: Newton at fixed w_1 = omega_start
+    double w = o->omega_start, rn = 0.0, zn = 0.0;
+    cudaEventRecord(c->ev[4], c->stream);
+    cudaMemcpyAsync(c->d.Z0, Z_start, m * 8, cudaMemcpyHostToDevice, c->stream);
+    int it = 0, evals = 1;
+    int st = eval_at_iterate(c, w, 1, &rn, &zn);
+    while (st >= FSE_ENOCONV && rn > o->rel_tol * zn && it < o->max_newton) {
+        rc = newton_solve_update(c);
+        if (rc && rc != FSE_ENOCONV) {
+            cleanup();
+            return rc;
+        }
+        ++it;
+        st = eval_at_iterate(c, w, 1, &rn, &zn);
+        ++evals;
+    }
+    int pst = (st < 0) ? st : (rn <= o->rel_tol * zn ? FSE_OK : FSE_ENOCONV);
+    record(0, w, it, evals, rn, zn, pst);
+    if (pst != FSE_OK) {
+        cleanup();
+        return pst;
+    }
+    // metric ||dZ||^2 + (sigma dw)^2 of the arclength
+    const double sigma = o->omega_scale > 0.0 ? o->omega_scale : zn / w;
+    const double s2 = sigma * sigma;
+    // ---- first tangent: [J dR/dw; 0 1] (t_Z; t_w) = (0; 1), oriented by `direction`
+    dRdw();
+    cudaMemsetAsync(tmp, 0, m * 8, c->stream);
+    fse::launch_bordered_jac(c, c->d.vec2, tmp, 1.0, c->Jd);
+    cudaMemsetAsync(rhs, 0, (m + 1) * 8, c->stream);
+    cudaStreamSynchronize(c->stream);
+    set_last(1.0);
+    rc = fse::dense_lu_solve(c, c->Jd, rhs, (int)m + 1);
+    if (rc) {
+        cleanup();
+        return set_err(c, rc, "singular bordered system at the start point");
+    }
+    double tw = get_last();
+    {
+        const double nrm = std::sqrt(sq_norm(rhs) + s2 * tw * tw);
+        const double sg = ((o->direction < 0) ? -1.0 : 1.0) * (tw < 0 ? -1.0 : 1.0) / nrm;
+        cudaMemcpyAsync(tZ, rhs, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+        fse::vec_axpby(c, m, 0.0, tZ, sg, tZ);
+        tw *= sg;
+    }
+    cudaMemcpyAsync(Zprev, c->d.Z0, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+    double wprev = w;
+    int worst = FSE_OK;
+    double ds = o->ds;
+    const double ds_max = std::max(o->ds_max, o->ds), ds_min = o->ds / 64.0;
+    for (int j = 1; j < o->n_points; ++j) {
+        cudaEventRecord(c->ev[4], c->stream);
+        // predictor: y_pred = y_{j-1} + ds t
+        const double wpred = wprev + ds * tw;
+        cudaMemcpyAsync(Zpred, Zprev, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+        fse::vec_axpby(c, m, ds, tZ, 1.0, Zpred);
+        cudaMemcpyAsync(c->d.Z0, Zpred, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+        w = wpred;
+        it = 0;
+        evals = 1;
+        st = eval_at_iterate(c, w, 1, &rn, &zn);
+        // corrector: Newton on R = 0 and t . (y - y_pred) = 0 (bordered system)
+        while (st >= FSE_ENOCONV && std::isfinite(rn) && rn > o->rel_tol * zn && it < o->max_newton) {
+            dRdw();
+            cudaMemcpyAsync(tmp, c->d.Z0, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+            fse::vec_axpby(c, m, -1.0, Zpred, 1.0, tmp);
+            const double Nres = dot(tZ, tmp) + s2 * tw * (w - wpred);
+            fse::launch_bordered_jac(c, c->d.vec2, tZ, s2 * tw, c->Jd);
+            fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, rhs);
+            cudaStreamSynchronize(c->stream);
+            set_last(-Nres);
+            rc = fse::dense_lu_solve(c, c->Jd, rhs, (int)m + 1);
+            if (rc) {
+                st = set_err(c, rc, "singular bordered system");
+                break;
+            }
+            const double dw = get_last();
+            fse::vec_axpby(c, m, 1.0, rhs, 1.0, c->d.Z0);
+            w += dw;
+            ++it;
+            st = eval_at_iterate(c, w, 1, &rn, &zn);
+            ++evals;
+        }
+        pst = (st < 0) ? st : ((std::isfinite(rn) && rn <= o->rel_tol * zn) ? FSE_OK : FSE_ENOCONV);
+        if (pst == FSE_ENOCONV && ds * 0.5 >= ds_min) {
+            // not converged from this prediction: halve the step and predict again from y_{j-1}
+            ds *= 0.5;
+            --j;
+            continue;
+        }
+        record(j, w, it, evals, rn, zn, pst);
+        if (pst != FSE_OK) {
+            worst = pst;
+            break;
+        }
+        // step control: grow after an easy correction, shrink after a hard one
+        if (it <= 2)
+            ds = std::min(ds * 1.5, ds_max);
+        else if (it >= 5)
+            ds = std::max(ds * 0.7, ds_min);
+        // secant tangent through the last two points
+        cudaMemcpyAsync(tZ, c->d.Z0, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+        fse::vec_axpby(c, m, -1.0, Zprev, 1.0, tZ);
+        tw = w - wprev;
+        const double nrm = std::sqrt(sq_norm(tZ) + s2 * tw * tw);
+        fse::vec_axpby(c, m, 0.0, tZ, 1.0 / nrm, tZ);
+        tw /= nrm;
+        cudaMemcpyAsync(Zprev, c->d.Z0, m * 8, cudaMemcpyDeviceToDevice, c->stream);
+        wprev = w;
+        if ((o->omega_max > 0.0 && w > o->omega_max) || w < o->omega_min) break;
+    }
+    cleanup();
+    return worst;
+}
+
 extern "C" int fse_set_steps(fse_ctx* c, int n_steps) {
     if (!c || n_steps < 0) return FSE_EINVAL;
     c->n_steps = n_steps;

@@ -197,6 +197,8 @@ void launch_domega(fse_ctx* c, double* zout);
 void launch_phi_copy(fse_ctx* c, double* Phi_dev, double* dzdw_dev);
 void launch_phi_copy_one(fse_ctx* c, int s, double* Phi_dev, double* dzdw_dev);
 void launch_dense_jac(fse_ctx* c, double* J);
+// (m + 1) x (m + 1) pseudo-arclength matrix [J dR/dw_1; t_Z^T tail] (row-major)
+void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double tail, double* B);
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
 // same propagation with the static device scratch of fse_aft.cu (no allocation)

@@ -465,6 +465,37 @@ class fse_cont_point(ctypes.Structure):
                 ("status", ctypes.c_int), ("predictor", ctypes.c_int)]
 
 
+class fse_arc_opts(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int), ("omega_start", ctypes.c_double), ("ds", ctypes.c_double),
+                ("ds_max", ctypes.c_double), ("omega_scale", ctypes.c_double), ("direction", ctypes.c_int), ("rel_tol", ctypes.c_double),
+                ("max_newton", ctypes.c_int), ("omega_min", ctypes.c_double), ("omega_max", ctypes.c_double)]
+
+
+def fse_continue_arclength(ctx, Z_start, omega_start, ds, n_points, direction=1, omega_scale=0.0,
+                           rel_tol=1e-10, max_newton=12, omega_min=0.0, omega_max=0.0, ds_max=0.0):
+    """fse_continue_arclength(): returns (Z (n_done x nu), omegas (n_done), list of dicts, rc)."""
+    lib = load()
+    if not hasattr(lib, "_arc_sig"):
+        lib.fse_continue_arclength.restype = ctypes.c_int
+        lib.fse_continue_arclength.argtypes = [_VP, ctypes.POINTER(fse_arc_opts), _DP, _DP, _DP,
+                                               ctypes.POINTER(fse_cont_point), _IP]
+        lib._arc_sig = True
+    o = fse_arc_opts(int(n_points), float(omega_start), float(ds), float(ds_max), float(omega_scale),
+                     int(direction),
+                     float(rel_tol), int(max_newton), float(omega_min), float(omega_max))
+    Z0 = np.ascontiguousarray(Z_start, dtype=np.float64)
+    Zout = np.zeros((n_points, Z0.size))
+    om = np.zeros(n_points)
+    info = (fse_cont_point * n_points)()
+    nd = np.zeros(1, np.int32)
+    rc = lib.fse_continue_arclength(ctx.h, ctypes.byref(o), _dp(Z0), _dp(Zout), _dp(om), info, _ip(nd))
+    if rc not in (FSE_OK, FSE_ENOCONV):
+        raise FSEError(rc, fse_last_error(ctx.h))
+    k = int(nd[0])
+    pts = [{f: getattr(info[j], f) for f, _ in fse_cont_point._fields_} for j in range(k)]
+    return Zout[:k], om[:k], pts, rc
+
+
 def fse_continue(ctx, omegas, Z_start, predictor="secant", mlp=None, rel_tol=1e-10, max_newton=10,
                  warmup=8, pod_modes=64, pod_every=8, train_steps=200, lr=1e-3, omega_range=None,
                  chord=False):
