@@ -614,7 +614,11 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
     constexpr int RT = 8;                          // rows per thread
     const int n = A.n, b = A.b, ld = A.ld, RM = A.RWT - 1, RECE = A.RECE, nblk = A.nblk;
     const int s = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rg = warp & 3, cg = warp >> 2;
+    // Row group of a warp: the zeros of the band tile and of the diagonal-block inverse are
+    // skipped, so the row groups do unequal work (FWD: 86 - 8 rg band columns and 8 + 8 rg
+    // diagonal ones); the second column half takes the row groups in reverse order, so the
+    // two warps that share a scheduler (warp and warp + 4) always do the same work in total.
+    const int cg = warp >> 2, rg = cg ? 3 - (warp & 3) : (warp & 3);
     const int r0 = RT * rg;                        // first row of this thread in the block
     const int cl = cg * (CW / 2) + EL * lane;      // first column of this thread in the tile
     const int t = blockIdx.x * CW + cl;            // global column
@@ -682,9 +686,12 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
         if (q + 1 < nblk) load_rows(Y, blk(q + 1), ynext);
         const bool wok = mbar_wait(&bar[buf], (q >> 1) & 1, A.err);
         const unsigned sL = sRec0 + (buf ? recb : 0u) + r0 * TS;     // this thread's 8 rows of the record
-        // band part: rows of earlier (FWD) or later (BWD) blocks from the ring
-        const int c0 = FWD ? max(0, b - i0) : 0;
-        const int c1 = FWD ? b : min(b, n - (i0 + FSE_BLK));
+        // band part: rows of earlier (FWD) or later (BWD) blocks from the ring.  Record column c
+        // is zero for row r when c < r (FWD: L(i0 + r, i0 - b + c) lies outside the band) or when
+        // c > b - 32 + r (BWD: L(i0 + 32 + c, i0 + r)), so this thread's rows r0 .. r0 + 7 need
+        // c >= r0 (FWD) or c < b - 24 + r0 (BWD) only.
+        const int c0 = FWD ? max(max(0, b - i0), r0) : 0;
+        const int c1 = FWD ? b : min(min(b, n - (i0 + FSE_BLK)), b - FSE_BLK + RT + r0);
         for (int c = c0; c < c1; ++c) {
             const int rowg = FWD ? (i0 - b + c) : (i0 + FSE_BLK + c);
             T xv[EL], lv[RT];
@@ -709,17 +716,23 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
         for (int rr = 0; rr < RT; ++rr)
 #pragma unroll
             for (int e = 0; e < EL; ++e) out[rr][e] = T(0);
+        // Dinv is lower triangular: row r takes k <= r (FWD, D'[k][r] = Dinv[r][k]) or k >= r
+        // (BWD, D'[k][r] = Dinv[k][r]), so this thread needs k < r0 + 8 (FWD) or k >= r0 (BWD)
         const unsigned sD = sL + dofs * TS;
-#pragma unroll 4
-        for (int k = 0; k < FSE_BLK; ++k) {
-            T tv[EL], dv[RT];
-            lds_vec<T>(sStg + (k * CW + cl) * TS, tv);
+        const int k0 = FWD ? 0 : r0, k1 = FWD ? r0 + RT : FSE_BLK;
+        for (int kb = k0; kb < k1; kb += RT) {
 #pragma unroll
-            for (int j = 0; j < RT / EL; ++j) lds_vec<T>(sD + (k * FSE_BLK + EL * j) * TS, dv + EL * j);
+            for (int kk = 0; kk < RT; ++kk) {
+                const int k = kb + kk;
+                T tv[EL], dv[RT];
+                lds_vec<T>(sStg + (k * CW + cl) * TS, tv);
 #pragma unroll
-            for (int rr = 0; rr < RT; ++rr)
+                for (int j = 0; j < RT / EL; ++j) lds_vec<T>(sD + (k * FSE_BLK + EL * j) * TS, dv + EL * j);
 #pragma unroll
-                for (int e = 0; e < EL; ++e) out[rr][e] += dv[rr] * tv[e];
+                for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+                    for (int e = 0; e < EL; ++e) out[rr][e] += dv[rr] * tv[e];
+            }
         }
 #pragma unroll
         for (int rr = 0; rr < RT; ++rr) {
