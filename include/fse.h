@@ -93,6 +93,11 @@ typedef struct fse_ctx fse_ctx;
  * Allocates all device memory of the context.  Errors: FSE_EINVAL for bad
  * sizes, the sampling rule S_j >= 2 H_j + 1 (Sec. 3.1), e > d, an element dof
  * out of range or a non-positive-definite M (FSE_ENONPOS_PIVOT); FSE_ENOMEM.
+ * FSE_EINVAL also when the model exceeds the kernels' on-chip working set
+ * (message "n or half-bandwidth too large for the on-chip working set"):
+ * b > 224, or b > 96 with FSE_FP64 tangents (the solves keep b + 32 solved rows
+ * of 128 or 256 columns in shared memory), or n beyond the state kernel's
+ * shared-memory vectors (about n > 3600 mixed, n > 2700 FP64, at b near 90).
  * On error *out is NULL.  device < 0 uses the current device. */
 int fse_setup(const fse_model* model, const fse_opts* opts, int device, fse_ctx** out);
 

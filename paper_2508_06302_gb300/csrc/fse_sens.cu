@@ -679,11 +679,19 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
         for (int rr = 0; rr < RT; ++rr)
 #pragma unroll
             for (int e = 0; e < EL; ++e) acc[rr][e] = ynext[rr][e];
-        if (!FWD) {
-            load_rows(X, B, xo);
-            load_rows(V, B, vo);
-        }
         if (q + 1 < nblk) load_rows(Y, blk(q + 1), ynext);
+        // BWD: X_k and V_k rows of the next block go to L2 now, so that their loads after the
+        // next band part hit L2
+        if (!FWD && q + 1 < nblk && tok) {
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) {
+                const int i = blk(q + 1) * FSE_BLK + r0 + rr;
+                if (i < n) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(X + (size_t)i * ld + t));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(V + (size_t)i * ld + t));
+                }
+            }
+        }
         const bool wok = mbar_wait(&bar[buf], (q >> 1) & 1, A.err);
         const unsigned sL = sRec0 + (buf ? recb : 0u) + r0 * TS;     // this thread's 8 rows of the record
         // band part: rows of earlier (FWD) or later (BWD) blocks from the ring.  Record column c
@@ -692,16 +700,36 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
         // c >= r0 (FWD) or c < b - 24 + r0 (BWD) only.
         const int c0 = FWD ? max(max(0, b - i0), r0) : 0;
         const int c1 = FWD ? b : min(min(b, n - (i0 + FSE_BLK)), b - FSE_BLK + RT + r0);
-        for (int c = c0; c < c1; ++c) {
+        // the operands of column c + 1 are read from shared memory before the products of column c
+        auto ldc = [&](int c, T xv[EL], T lv[RT]) {
             const int rowg = FWD ? (i0 - b + c) : (i0 + FSE_BLK + c);
-            T xv[EL], lv[RT];
             lds_vec<T>(sRing + (unsigned)(rowg & RM) * (CW * TS), xv);
 #pragma unroll
             for (int k = 0; k < RT / EL; ++k) lds_vec<T>(sL + (c * FSE_BLK + EL * k) * TS, lv + EL * k);
+        };
+        auto fmc = [&](const T xv[EL], const T lv[RT]) {
 #pragma unroll
             for (int rr = 0; rr < RT; ++rr)
 #pragma unroll
                 for (int e = 0; e < EL; ++e) acc[rr][e] -= lv[rr] * xv[e];
+        };
+        {
+            T xa[EL], la[RT], xb[EL], lb[RT];
+            int c = c0;
+            if (c < c1) ldc(c, xa, la);
+            for (; c + 1 < c1; c += 2) {
+                ldc(c + 1, xb, lb);
+                fmc(xa, la);
+                if (c + 2 < c1) ldc(c + 2, xa, la);
+                fmc(xb, lb);
+            }
+            if (c < c1) fmc(xa, la);
+        }
+        // X_k and V_k of the block (for the V update) are read after the band part: fewer live
+        // registers during it, and still a whole diagonal step ahead of their use
+        if (!FWD) {
+            load_rows(X, B, xo);
+            load_rows(V, B, vo);
         }
 #pragma unroll
         for (int rr = 0; rr < RT; ++rr) sts_vec<T>(sStg + ((r0 + rr) * CW + cl) * TS, acc[rr]);

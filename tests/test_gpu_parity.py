@@ -30,6 +30,8 @@ CASES = {
     "beam18_d2": (lambda: I.eb_beam(), 2, [16], [7], 64, [I.GOLDEN], 1.1, 1e-3),
     "vk87_d2": (lambda: I.vk_beam(n_el=30, F1=1.0, F2=1.0), 2, [5], [2], 48, [I.GOLDEN], 1.1, 1e-6),
     "shell90_d2": (lambda: I.flat_shell(nx=6, ny=4), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
+    # half-bandwidth 110 > 96: the tangent solves take the wide-band kernel (k_trsm)
+    "shell204_wide_d2": (lambda: I.flat_shell(nx=3, ny=18), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
     "chain5_d3": (lambda: I.chain(5, F=(1.0, 0.5, 0.3)), 3, [3, 5], [1, 2], 16,
                   [math.sqrt(2), math.sqrt(3)], 1.1, 1e-3),
     "chain4_d3_e1": (lambda: I.chain(4, F=(1.0,)), 3, [3, 3], [1, 1], 12, [0.37, 0.71], 1.2, 1e-3),
@@ -52,7 +54,11 @@ def _setup(name, precision="fp64", maxit=16):
     return m, prob, ctx, Z, w1
 
 
-@pytest.mark.parametrize("name", list(CASES))
+# FP64 tangents with b > 96 do not fit the solves' shared-memory ring (tested below)
+FP64_CASES = [c for c in CASES if c != "shell204_wide_d2"]
+
+
+@pytest.mark.parametrize("name", FP64_CASES)
 def test_residual_and_monodromy_fp64(name):
     m, prob, ctx, Z, w1 = _setup(name)
     ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=16)
@@ -65,6 +71,14 @@ def test_residual_and_monodromy_fp64(name):
         np.testing.assert_allclose(Phi[s], ref.Phi[s], rtol=0, atol=1e-10 * np.abs(ref.Phi[s]).max())
         np.testing.assert_allclose(dz[s], ref.dz_dw[s], rtol=0, atol=1e-10 * np.abs(ref.dz_dw[s]).max())
     ctx.close()
+
+
+def test_wide_band_fp64_is_rejected_at_setup():
+    mk = CASES["shell204_wide_d2"][0]
+    fse = _fse()
+    with pytest.raises(fse.FSEError) as ei:
+        fse.Context(mk(), 2, [5], [2], [I.GOLDEN], 20, precision="fp64")
+    assert ei.value.code == fse.FSE_EINVAL and "on-chip working set" in str(ei.value)
 
 
 @pytest.mark.parametrize("name", ["beam18_d2", "shell90_d2", "chain5_d3"])
@@ -84,7 +98,7 @@ def test_jacobian_products_fp64(name):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "chain5_d3"])
+@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "shell204_wide_d2", "chain5_d3"])
 def test_mixed_fp32(name):
     m, prob, ctx, Z, w1 = _setup(name, precision="mixed_fp32", maxit=16)
     ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=16)
