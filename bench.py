@@ -17,6 +17,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -100,7 +101,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples are kept beside the run's other outputs (FSE_BENCH_OUT), else in /tmp
+        out_dir = os.environ.get("FSE_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         try:
