@@ -207,10 +207,19 @@ def step_work(m, N, band, ld, prec_bytes):
     }
 
 
+def kernel_source_hash():
+    """Hash of the tangent kernels' device code: fse_sens.cu up to its host launchers, plus the
+    device helpers of fse_common.cuh (a change in host code leaves it unchanged)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2508_06302_gb300", "csrc")
+    dev = open(os.path.join(csrc, "fse_sens.cu")).read().split("// launchers", 1)[0]
+    dev += open(os.path.join(csrc, "fse_common.cuh")).read()
+    return hashlib.sha256(dev.encode()).hexdigest()[:16]
+
+
 def recorded_traffic(kernel, workload_name):
     """DRAM bytes per launch recorded by an ncu capture in profiles/, with the hash of the
     kernel sources it was taken on; None when absent or when the sources changed since."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload_name))
     if not os.path.exists(path):
         return None
@@ -219,8 +228,7 @@ def recorded_traffic(kernel, workload_name):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             rec[k.strip()] = v.strip().strip("`")
-    src = os.path.join(ROOT, "paper_2508_06302_gb300", "csrc", "fse_sens.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     if rec.get("sources_sha256_16") != h:
         return None
     try:

@@ -4,6 +4,7 @@
 #include <cuda.h>   // CUtensorMap (types only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -181,6 +182,20 @@ int make_tangent_maps(fse_ctx* c);
 
 // launchers
 void ensure_constants();
+
+// One-time set-up per device (kernel attributes, __constant__ tables): true while the current
+// device's bit of `done` is clear.  The caller runs its set-up and then calls mark_device; two
+// threads racing on a first use both run the (idempotent) set-up.
+inline bool needs_device_setup(const std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return (done.load() & (1ull << (dev & 63))) == 0;
+}
+inline void mark_device(std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    done.fetch_or(1ull << (dev & 63));
+}
 void launch_fill_tables(fse_ctx* c);
 void launch_build_ops(fse_ctx* c, double omega1);
 void launch_build_groups(fse_ctx* c);

@@ -813,16 +813,17 @@ int make_tangent_maps(fse_ctx* c) {
     using encode_fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static encode_fn encode = nullptr;
-    if (!encode) {
+    // the driver's encoder, looked up once per process (thread-safe static initialisation)
+    static const encode_fn encode = []() -> encode_fn {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return FSE_ECUDA;
-        encode = reinterpret_cast<encode_fn>(fn);
-    }
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<encode_fn>(fn);
+    }();
+    if (!encode) return FSE_ECUDA;
     const Params& p = c->p;
     const bool f32 = p.prec == FSE_MIXED_FP32;
     const size_t tsz = f32 ? 4 : 8;
@@ -857,10 +858,10 @@ void launch_build_groups(fse_ctx* c) {
 
 template <typename T, int R>
 static void rhs_launch(fse_ctx* c, const SensArgs& A, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    if (needs_device_setup(attr)) {
         cudaFuncSetAttribute(k_sens_rhs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
+        mark_device(attr);
     }
     const Params& p = c->p;
     constexpr int CW = sizeof(T) == 4 ? 64 : 32;
@@ -880,13 +881,13 @@ size_t trsm_smem(const Params& p) {
 template <typename T>
 static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t st) {
     const Params& p = c->p;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    if (needs_device_setup(attr)) {
         cudaFuncSetAttribute(k_trsm<T, true, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, true, 28>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, false, 28>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
+        mark_device(attr);
     }
     if (phase == 0) {
         switch (p.R) {
@@ -896,11 +897,11 @@ static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t s
             default: rhs_launch<T, 4>(c, A, st); break;
         }
     } else if (p.b <= 96) {
-        static bool attr8 = false;
-        if (!attr8) {
+        static std::atomic<unsigned long long> attr8{0};
+        if (needs_device_setup(attr8)) {
             cudaFuncSetAttribute(k_trsm8<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
             cudaFuncSetAttribute(k_trsm8<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            attr8 = true;
+            mark_device(attr8);
         }
         constexpr int CW = 64 * (16 / (int)sizeof(T));
         dim3 g((p.P + CW - 1) / CW, p.N);

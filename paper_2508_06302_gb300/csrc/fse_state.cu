@@ -11,10 +11,10 @@
 
 namespace fse {
 
-static bool g_const_ready = false;
+static std::atomic<unsigned long long> g_const_ready{0};   // per device (bit = device id)
 
 void ensure_constants() {
-    if (g_const_ready) return;
+    if (!needs_device_setup(g_const_ready)) return;
     // closed forms of the 5-point Gauss-Legendre rule
     const double r = 2.0 * sqrt(10.0 / 7.0);
     double x[5] = {-sqrt(5.0 + r) / 3.0, -sqrt(5.0 - r) / 3.0, 0.0, sqrt(5.0 - r) / 3.0,
@@ -24,7 +24,7 @@ void ensure_constants() {
                    (322.0 + s70) / 900.0, (322.0 - s70) / 900.0};
     cudaMemcpyToSymbol(c_glx, x, sizeof(x));
     cudaMemcpyToSymbol(c_glw, w, sizeof(w));
-    g_const_ready = true;
+    mark_device(g_const_ready);
 }
 
 // ----------------------------------------------------------------------------
@@ -881,10 +881,10 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
 
 template <typename T>
 static void state_launch(fse_ctx* c, const StateArgs& A, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_set{0};
+    if (needs_device_setup(attr_set)) {
         cudaFuncSetAttribute(k_state<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
+        mark_device(attr_set);
     }
     k_state<T><<<c->p.N, 256, c->p.smem_state, st>>>(A);
 }
