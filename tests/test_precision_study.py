@@ -29,16 +29,21 @@ def _round(x, p):
 
 def _tangent_monodromy(model, w, p_op):
     """Phi = [X; V][:, :2n] after S1 steps of the Eq. E8 recurrence (f_nl = 0), operands of
-    every product rounded to p_op bits, results to FP32 (FP64 throughout when p_op = 53)."""
+    every product rounded to p_op bits, or split into two TF32 parts ("3xtf32"), results to
+    FP32 (FP64 throughout when p_op = 53)."""
     n = model.n
     Dl = 2.0 * np.pi / S1
     a0c, a1c, a2c = 4.0 / Dl ** 2, 4.0 / Dl, 2.0 / Dl
     M, D, K = model.M, model.D, model.K
     wM = w * w * M
     Keff_inv = np.linalg.inv(wM * a0c + w * a2c * D + K)
-    st = (lambda x: x) if p_op >= 53 else (lambda x: _round(x, 24))
+    st = (lambda x: x) if p_op == 53 else (lambda x: _round(x, 24))
 
     def mm(A, B):
+        if p_op == "3xtf32":   # split operands a = hi + lo, both TF32; the lo*lo term dropped
+            Ah, Bh = _round(A, 11), _round(B, 11)
+            Al, Bl = _round(A - Ah, 11), _round(B - Bh, 11)
+            return st(Ah @ Bh + (Ah @ Bl + Al @ Bh))
         return st(_round(A, p_op) @ _round(B, p_op))
 
     X = np.zeros((n, 2 * n))
@@ -73,11 +78,13 @@ def test_fp32_tangents_keep_newton_contracting_tf32_and_bf16_do_not():
     # the harness in FP64 is the oracle's recurrence
     assert np.linalg.norm(_tangent_monodromy(m, w, 53) - ref) <= 1e-11 * nref
     err, con = {}, {}
-    for name, p in (("fp32", 24), ("tf32", 11), ("bf16", 8)):
+    for name, p in (("fp32", 24), ("tf32", 11), ("bf16", 8), ("3xtf32", "3xtf32")):
         P = _tangent_monodromy(m, w, p)
         err[name] = np.linalg.norm(P - ref) / nref
         con[name] = _contraction(ref, P - ref, I.GOLDEN)
-    # measured: fp32 2.0e-5 / 0.008, tf32 0.28 / 128, bf16 1.7 / 127
+    # measured: fp32 2.0e-5 / 0.008, tf32 0.28 / 128, bf16 1.7 / 127, 3xtf32 6.4e-5 / 0.019
     assert err["fp32"] < 1e-4 and con["fp32"] < 0.05, (err, con)
     assert err["tf32"] > 0.05 and con["tf32"] > 1.0, (err, con)
     assert err["bf16"] > 0.5 and con["bf16"] > 1.0, (err, con)
+    # a split (3 x TF32) product recovers FP32-level tangents
+    assert err["3xtf32"] < 1e-4 and con["3xtf32"] < 0.05, (err, con)
