@@ -328,6 +328,17 @@ def continuation_points(fse, ctx, wl, K, predictor="secant", device=0):
             "omega1_over_wn1": [round(float(w / w_n1), 4) for w in omegas]}
 
 
+def half_bandwidth(model):
+    """Half-bandwidth of the union pattern of M, D, K and the nonlinear elements' dof spans."""
+    i, j = np.nonzero((model.M != 0) | (model.D != 0) | (model.K != 0))
+    b = int(np.max(np.abs(i - j))) if i.size else 0
+    for dofs in model.nl_dof:
+        d = [int(x) for x in dofs if x >= 0]
+        if len(d) > 1:
+            b = max(b, max(d) - min(d))
+    return b
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -349,7 +360,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "n": wl.model.n, "N": wl.N,
-                                            "H": wl.H, "S1": wl.S1},
+                                            "H": wl.H, "S1": wl.S1, "band": half_bandwidth(wl.model),
+                                            "precision": "fp64 (oracle)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
                              "kind": "oracle", "sample": samples[0]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
