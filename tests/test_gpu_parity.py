@@ -30,6 +30,11 @@ CASES = {
     "beam18_d2": (lambda: I.eb_beam(), 2, [16], [7], 64, [I.GOLDEN], 1.1, 1e-3),
     "vk87_d2": (lambda: I.vk_beam(n_el=30, F1=1.0, F2=1.0), 2, [5], [2], 48, [I.GOLDEN], 1.1, 1e-6),
     "shell90_d2": (lambda: I.flat_shell(nx=6, ny=4), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
+    # degenerate torus: one trajectory, the constant harmonic only (periodic forcing, Sec. 3.1
+    # reduction to classical shooting)
+    "chain4_N1_H0": (lambda: I.chain(4, F=(2.0, 0.0), c=3.0), 2, [1], [0], 24, [I.GOLDEN], 1.2, 1e-3),
+    # one dof (half-bandwidth 0): every tile of the solves is ragged
+    "chain1_n1": (lambda: I.chain(1), 2, [5], [2], 24, [I.GOLDEN], 1.1, 1e-3),
     # half-bandwidth 110 > 96: the tangent solves take the wide-band kernel (k_trsm)
     "shell204_wide_d2": (lambda: I.flat_shell(nx=3, ny=18), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
     "chain5_d3": (lambda: I.chain(5, F=(1.0, 0.5, 0.3)), 3, [3, 5], [1, 2], 16,
@@ -81,7 +86,7 @@ def test_wide_band_fp64_is_rejected_at_setup():
     assert ei.value.code == fse.FSE_EINVAL and "on-chip working set" in str(ei.value)
 
 
-@pytest.mark.parametrize("name", ["beam18_d2", "shell90_d2", "chain5_d3"])
+@pytest.mark.parametrize("name", ["beam18_d2", "shell90_d2", "chain5_d3", "chain4_N1_H0"])
 def test_jacobian_products_fp64(name):
     m, prob, ctx, Z, w1 = _setup(name)
     ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=True, tol=0, maxit=16)
@@ -98,7 +103,8 @@ def test_jacobian_products_fp64(name):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "shell204_wide_d2", "chain5_d3"])
+@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "shell204_wide_d2", "chain5_d3",
+                                  "chain4_N1_H0", "chain1_n1"])
 def test_mixed_fp32(name):
     m, prob, ctx, Z, w1 = _setup(name, precision="mixed_fp32", maxit=16)
     ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=16)
