@@ -598,6 +598,19 @@ __device__ __forceinline__ void sts_vec(unsigned a, const T v[16 / sizeof(T)]) {
         asm volatile("st.shared.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(v[0]), "d"(v[1]) : "memory");
 }
 
+// packed FP32 pair helpers (fma.rn.f32x2: two IEEE fused multiply-adds per instruction)
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ void fma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 // Blocked banded substitution with 8 x EL register tiles (b <= 96): one CTA = one trajectory
 // x CW = 64 EL directions (256 in FP32, 128 in FP64), 8 warps = 4 row groups of 8 rows x 2
 // column halves.  Each shared-memory read of a solved row feeds 8 rows.  The factor of the
@@ -607,6 +620,9 @@ __device__ __forceinline__ void sts_vec(unsigned a, const T v[16 / sizeof(T)]) {
 //  FWD: y_B = Dinv_B (rhs_B - L_{B,<} y_<)      record Rf = [L(i0 + r, i0 - b + c) | Dinv^T]
 //  BWD: x_B = Dinv_B^T (y_B - L_{>,B}^T x_>)    record Rb = [L(i0 + 32 + c, i0 + r) | Dinv]
 //       then X <- x, V <- 2/D (x - X) - V.
+// FP32: the products run as packed pairs of rows (fma.rn.f32x2, two IEEE FMAs per instruction,
+// the same results as scalar FMAs with half the issue slots); the ring holds -x so that the band
+// update is one packed FMA per pair.
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
     constexpr int EL = 16 / sizeof(T);             // columns per lane
@@ -707,11 +723,28 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
 #pragma unroll
             for (int k = 0; k < RT / EL; ++k) lds_vec<T>(sL + (c * FSE_BLK + EL * k) * TS, lv + EL * k);
         };
+        // FP32: accumulators in row pairs, the ring holds -y, so one packed FMA gives acc - l y
+        unsigned long long A2[RT / 2][EL];
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int p2 = 0; p2 < RT / 2; ++p2)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) A2[p2][e] = pk2(acc[2 * p2][e], acc[2 * p2 + 1][e]);
+        }
         auto fmc = [&](const T xv[EL], const T lv[RT]) {
+            if constexpr (sizeof(T) == 4) {
 #pragma unroll
-            for (int rr = 0; rr < RT; ++rr)
+                for (int e = 0; e < EL; ++e) {
+                    const unsigned long long xd = pk2(xv[e], xv[e]);
 #pragma unroll
-                for (int e = 0; e < EL; ++e) acc[rr][e] -= lv[rr] * xv[e];
+                    for (int p2 = 0; p2 < RT / 2; ++p2) fma2(A2[p2][e], pk2(lv[2 * p2], lv[2 * p2 + 1]), xd);
+                }
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+                    for (int e = 0; e < EL; ++e) acc[rr][e] -= lv[rr] * xv[e];
+            }
         };
         {
             T xa[EL], la[RT], xb[EL], lb[RT];
@@ -724,6 +757,12 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
                 fmc(xb, lb);
             }
             if (c < c1) fmc(xa, la);
+        }
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int p2 = 0; p2 < RT / 2; ++p2)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) upk2(A2[p2][e], acc[2 * p2][e], acc[2 * p2 + 1][e]);
         }
         // X_k and V_k of the block (for the V update) are read after the band part: fewer live
         // registers during it, and still a whole diagonal step ahead of their use
@@ -748,6 +787,13 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
         // (BWD, D'[k][r] = Dinv[k][r]), so this thread needs k < r0 + 8 (FWD) or k >= r0 (BWD)
         const unsigned sD = sL + dofs * TS;
         const int k0 = FWD ? 0 : r0, k1 = FWD ? r0 + RT : FSE_BLK;
+        unsigned long long O2[RT / 2][EL];
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int p2 = 0; p2 < RT / 2; ++p2)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) O2[p2][e] = 0ull;
+        }
         for (int kb = k0; kb < k1; kb += RT) {
 #pragma unroll
             for (int kk = 0; kk < RT; ++kk) {
@@ -756,16 +802,38 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
                 lds_vec<T>(sStg + (k * CW + cl) * TS, tv);
 #pragma unroll
                 for (int j = 0; j < RT / EL; ++j) lds_vec<T>(sD + (k * FSE_BLK + EL * j) * TS, dv + EL * j);
+                if constexpr (sizeof(T) == 4) {
 #pragma unroll
-                for (int rr = 0; rr < RT; ++rr)
+                    for (int e = 0; e < EL; ++e) {
+                        const unsigned long long td = pk2(tv[e], tv[e]);
 #pragma unroll
-                    for (int e = 0; e < EL; ++e) out[rr][e] += dv[rr] * tv[e];
+                        for (int p2 = 0; p2 < RT / 2; ++p2) fma2(O2[p2][e], pk2(dv[2 * p2], dv[2 * p2 + 1]), td);
+                    }
+                } else {
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+                        for (int e = 0; e < EL; ++e) out[rr][e] += dv[rr] * tv[e];
+                }
             }
+        }
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int p2 = 0; p2 < RT / 2; ++p2)
+#pragma unroll
+                for (int e = 0; e < EL; ++e) upk2(O2[p2][e], out[2 * p2][e], out[2 * p2 + 1][e]);
         }
 #pragma unroll
         for (int rr = 0; rr < RT; ++rr) {
             const int i = i0 + r0 + rr;
-            sts_vec<T>(sRing + (unsigned)(i & RM) * (CW * TS), out[rr]);
+            if constexpr (sizeof(T) == 4) {
+                T ng[EL];
+#pragma unroll
+                for (int e = 0; e < EL; ++e) ng[e] = -out[rr][e];
+                sts_vec<T>(sRing + (unsigned)(i & RM) * (CW * TS), ng);
+            } else {
+                sts_vec<T>(sRing + (unsigned)(i & RM) * (CW * TS), out[rr]);
+            }
             if (i < n && tok) {
                 const size_t o = (size_t)i * ld + t;
                 if (FWD) {
