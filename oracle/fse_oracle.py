@@ -7,7 +7,7 @@ path: every function here is a direct, slow, step-by-step restatement of the
 paper's definitions in NumPy float64, written so that a reader can check it
 against the paper by eye.
 
-Conventions (readings of the paper, all listed in the design doc):
+Conventions (readings of the paper where it is silent or ambiguous):
 
 * The state is z = [q; u] with u = q' = dq/dphi_1 (App. E, Eq. E8), not the
   physical velocity of Eq. (2); Eq. (F3) converts for the Lyapunov part.
@@ -421,7 +421,7 @@ def residual_jacobian(prob, Z0, omega1, want_jacobian=True, dense=True, tol=1e-1
 
     With ``want_jacobian`` also returns the monodromy blocks and, if ``dense``,
     dR/dZ(0) of Eq. (22) and dR/dw_1 of Eq. (23) (rho fixed, so the rotation
-    term of Eq. 23 vanishes).
+    term of Eq. 23 vanishes: only the integration term remains).
     """
     n = prob.n
     zb0 = idft(prob, Z0)
