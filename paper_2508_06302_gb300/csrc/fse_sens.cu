@@ -881,7 +881,8 @@ int make_tangent_maps(fse_ctx* c) {
     using encode_fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    // the driver's encoder, looked up once per process (thread-safe static initialisation)
+    // cuTensorMapEncodeTiled from the CUDA driver API, looked up once per process (thread-safe static
+    // initialisation)
     static const encode_fn encode = []() -> encode_fn {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
