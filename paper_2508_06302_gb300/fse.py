@@ -131,6 +131,15 @@ def _ip(a: np.ndarray):
     return a.ctypes.data_as(_IP)
 
 
+def _f64_vector(a, size, what):
+    """Contiguous float64 copy-or-view of `a` with exactly `size` entries (ValueError otherwise):
+    the C side reads and writes whole vectors, so a short buffer must never reach it."""
+    v = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if v.size != size:
+        raise ValueError("%s: expected %d values, got %d" % (what, size, v.size))
+    return v
+
+
 class FSEError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("FSE error %d: %s" % (code, msg))
@@ -230,8 +239,7 @@ class Context:
 
     def residual_jacobian(self, Z0, omega1, want_jacobian=True, allow_status=(FSE_ENOCONV,)):
         """fse_residual_jacobian(): returns (R, traj_status, newton_iters, rc)."""
-        Z = np.ascontiguousarray(Z0, dtype=np.float64)
-        assert Z.size == self.n_unknowns
+        Z = _f64_vector(Z0, self.n_unknowns, "Z0")
         R = np.zeros(self.n_unknowns)
         st = np.zeros(self.N, np.int32)
         it = np.zeros(self.N, np.int32)
@@ -255,6 +263,8 @@ class Context:
 
     def jacobian_apply(self, V):
         V = np.ascontiguousarray(np.atleast_2d(V), dtype=np.float64)
+        if V.ndim != 2 or V.shape[1] != self.n_unknowns:
+            raise ValueError("V: expected rows of %d values, got shape %s" % (self.n_unknowns, V.shape))
         out = np.zeros_like(V)
         self._check(load().fse_jacobian_apply(self.h, _dp(V), _dp(out), V.shape[0]))
         return out
@@ -284,7 +294,7 @@ class Context:
         return Phi, dz
 
     def newton_step(self, Z0, omega1):
-        Z = np.ascontiguousarray(Z0, dtype=np.float64).copy()
+        Z = _f64_vector(Z0, self.n_unknowns, "Z0").copy()
         rn = ctypes.c_double()
         rc = load().fse_newton_step(self.h, _dp(Z), float(omega1), ctypes.byref(rn))
         self._check(rc, (FSE_ENOCONV,))
@@ -303,8 +313,10 @@ class Context:
         return it.value, rr.value
 
     def lyapunov(self, Z0, omega1, N_Ly, h):
-        Z = np.ascontiguousarray(Z0, dtype=np.float64)
-        out = np.zeros(h)
+        Z = _f64_vector(Z0, self.n_unknowns, "Z0")
+        if int(h) < 1:
+            raise ValueError("h must be >= 1")
+        out = np.zeros(int(h))
         rc = load().fse_lyapunov(self.h, _dp(Z), float(omega1), int(N_Ly), int(h), _dp(out))
         self._check(rc, (FSE_ENOCONV,))
         return out
@@ -312,8 +324,10 @@ class Context:
     def lyapunov_noalloc(self, Z0, omega1, N_Ly, h):
         """fse_lyapunov_noalloc: the exponents of `lyapunov` with no device
         allocation (static library scratch shared by every call)."""
-        Z = np.ascontiguousarray(Z0, dtype=np.float64)
-        out = np.zeros(h)
+        Z = _f64_vector(Z0, self.n_unknowns, "Z0")
+        if int(h) < 1:
+            raise ValueError("h must be >= 1")
+        out = np.zeros(int(h))
         rc = load().fse_lyapunov_noalloc(self.h, _dp(Z), float(omega1), int(N_Ly), int(h), _dp(out))
         self._check(rc, (FSE_ENOCONV,))
         return out
@@ -348,11 +362,13 @@ class Batch:
 
     def residual_jacobian(self, Z0s, omegas, want_jacobian=True):
         """Returns (list of R, status array, rc)."""
-        Zs = [np.ascontiguousarray(z, dtype=np.float64) for z in Z0s]
+        if len(Z0s) != len(self.ctx):
+            raise ValueError("Z0s: expected %d vectors, got %d" % (len(self.ctx), len(Z0s)))
+        Zs = [_f64_vector(z, c.n_unknowns, "Z0s[%d]" % i) for i, (z, c) in enumerate(zip(Z0s, self.ctx))]
         Rs = [np.zeros(c.n_unknowns) for c in self.ctx]
         zp = (_DP * len(Zs))(*[_dp(z) for z in Zs])
         rp = (_DP * len(Rs))(*[_dp(r) for r in Rs])
-        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        om = _f64_vector(omegas, len(self.ctx), "omegas")
         st = np.zeros(len(self.ctx), np.int32)
         rc = load().fse_batch_residual_jacobian(self.h, zp, _dp(om), rp, int(bool(want_jacobian)), _ip(st))
         if rc not in (FSE_OK, FSE_ENOCONV):
@@ -404,7 +420,8 @@ class Mlp:
     def set_params(self, params):
         flat = np.ascontiguousarray(np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
                                                     for k in self.ORDER]), dtype=np.float32)
-        assert flat.size == self.np
+        if flat.size != self.np:
+            raise ValueError("params: expected %d values, got %d" % (self.np, flat.size))
         self._check(load().fse_mlp_set_params(self.h, _fp(flat)))
 
     def get_params(self):
@@ -412,23 +429,32 @@ class Mlp:
         self._check(load().fse_mlp_get_params(self.h, _fp(flat)))
         return flat
 
-    def forward(self, X):
+    def _inputs(self, X, T=None):
         X = np.ascontiguousarray(X, dtype=np.float32)
+        if X.ndim != 2 or X.shape[1] != self.dims[0]:
+            raise ValueError("X: expected shape (B, %d), got %s" % (self.dims[0], X.shape))
+        if T is None:
+            return X
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        if T.shape != (X.shape[0], self.dims[2]):
+            raise ValueError("T: expected shape (%d, %d), got %s" % (X.shape[0], self.dims[2], T.shape))
+        return X, T
+
+    def forward(self, X):
+        X = self._inputs(X)
         Y = np.zeros((X.shape[0], self.dims[2]), np.float32)
         self._check(load().fse_mlp_forward(self.h, _fp(X), X.shape[0], _fp(Y)))
         return Y
 
     def grad(self, X, T):
-        X = np.ascontiguousarray(X, dtype=np.float32)
-        T = np.ascontiguousarray(T, dtype=np.float32)
+        X, T = self._inputs(X, T)
         loss = np.zeros(1, np.float32)
         g = np.zeros(self.np, np.float32)
         self._check(load().fse_mlp_grad(self.h, _fp(X), _fp(T), X.shape[0], _fp(loss), _fp(g)))
         return float(loss[0]), g
 
     def train(self, X, T, steps, lr):
-        X = np.ascontiguousarray(X, dtype=np.float32)
-        T = np.ascontiguousarray(T, dtype=np.float32)
+        X, T = self._inputs(X, T)
         loss = np.zeros(1, np.float32)
         self._check(load().fse_mlp_train(self.h, _fp(X), _fp(T), X.shape[0], int(steps), float(lr), _fp(loss)))
         return float(loss[0])
@@ -480,10 +506,12 @@ def fse_continue_arclength(ctx, Z_start, omega_start, ds, n_points, direction=1,
         lib.fse_continue_arclength.argtypes = [_VP, ctypes.POINTER(fse_arc_opts), _DP, _DP, _DP,
                                                ctypes.POINTER(fse_cont_point), _IP]
         lib._arc_sig = True
+    if int(n_points) < 1:
+        raise ValueError("n_points must be >= 1")
+    Z0 = _f64_vector(Z_start, ctx.n_unknowns, "Z_start")
     o = fse_arc_opts(int(n_points), float(omega_start), float(ds), float(ds_max), float(omega_scale),
                      int(direction),
                      float(rel_tol), int(max_newton), float(omega_min), float(omega_max))
-    Z0 = np.ascontiguousarray(Z_start, dtype=np.float64)
     Zout = np.zeros((n_points, Z0.size))
     om = np.zeros(n_points)
     info = (fse_cont_point * n_points)()
@@ -508,12 +536,14 @@ def fse_continue(ctx, omegas, Z_start, predictor="secant", mlp=None, rel_tol=1e-
         lib.fse_mlp_nouts.restype = ctypes.c_int
         lib.fse_mlp_nouts.argtypes = [_VP]
         lib._cont_sig = True
-    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    om = np.ascontiguousarray(omegas, dtype=np.float64).reshape(-1)
     P = om.size
+    if P < 1:
+        raise ValueError("omegas: at least one point")
     lo, hi = (float(om.min()), float(om.max())) if omega_range is None else omega_range
     o = fse_cont_opts(P, _dp(om), FSE_PRED_MLP if predictor == "mlp" else FSE_PRED_SECANT, rel_tol, max_newton,
                       warmup, pod_modes, pod_every, train_steps, lr, lo, hi, int(bool(chord)))
-    Z0 = np.ascontiguousarray(Z_start, dtype=np.float64)
+    Z0 = _f64_vector(Z_start, ctx.n_unknowns, "Z_start")
     Zout = np.zeros((P, Z0.size))
     info = (fse_cont_point * P)()
     rc = lib.fse_continue(ctx.h, mlp.h if mlp is not None else None, ctypes.byref(o), _dp(Z0), _dp(Zout), info)
