@@ -209,12 +209,15 @@ def step_work(m, N, band, ld, prec_bytes):
 
 def kernel_source_hash():
     """Hash of the tangent kernels' device code: fse_sens.cu up to its host launchers, plus the
-    device helpers of fse_common.cuh (a change in host code leaves it unchanged)."""
+    device helpers of fse_common.cuh, with // comments and whitespace removed (a change in host
+    code or in a comment leaves it unchanged, any change of the device code does not)."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_2508_06302_gb300", "csrc")
     dev = open(os.path.join(csrc, "fse_sens.cu")).read().split("// launchers", 1)[0]
     dev += open(os.path.join(csrc, "fse_common.cuh")).read()
-    return hashlib.sha256(dev.encode()).hexdigest()[:16]
+    code = re.sub(r"\s+", "", re.sub(r"//[^\n]*", "", dev))
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload_name):

@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
     const int n = A.n, b = A.b, ld = A.ld, RM = A.RWT - 1, RECE = A.RECE, nblk = A.nblk;
     const int s = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Row group of a warp: the zeros of the band tile and of the diagonal-block inverse are
-    // skipped, so the row groups do unequal work (FWD: 86 - 8 rg band columns and 8 + 8 rg
+    // skipped, so the row groups do unequal work (FWD: b - 8 rg band columns and 8 + 8 rg
     // diagonal ones); the second column half takes the row groups in reverse order, so the
     // two warps that share a scheduler (warp and warp + 4) always do the same work in total.
     const int cg = warp >> 2, rg = cg ? 3 - (warp & 3) : (warp & 3);
