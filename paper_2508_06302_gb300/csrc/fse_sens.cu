@@ -952,8 +952,6 @@ static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t s
     const Params& p = c->p;
     static std::atomic<unsigned long long> attr{0};
     if (needs_device_setup(attr)) {
-        cudaFuncSetAttribute(k_trsm<T, true, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        cudaFuncSetAttribute(k_trsm<T, false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, true, 28>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         cudaFuncSetAttribute(k_trsm<T, false, 28>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         mark_device(attr);
@@ -979,19 +977,13 @@ static void sens_launch(fse_ctx* c, const SensArgs& A, int phase, cudaStream_t s
         else
             k_trsm8<T, false><<<g, 256, p.smem_trsm, st>>>(A);
     } else {
+        // 96 < b <= FSE_MAX_BAND (224): the factor tile of b x 32 values over 256 threads needs
+        // MAXL = 28 registers per thread
         dim3 g((p.P + 127) / 128, p.N);
-        const bool small = p.b <= 96;   // factor tile of b x 32 spread over 256 threads
-        if (phase == 1) {
-            if (small)
-                k_trsm<T, true, 12><<<g, 256, p.smem_trsm, st>>>(A);
-            else
-                k_trsm<T, true, 28><<<g, 256, p.smem_trsm, st>>>(A);
-        } else {
-            if (small)
-                k_trsm<T, false, 12><<<g, 256, p.smem_trsm, st>>>(A);
-            else
-                k_trsm<T, false, 28><<<g, 256, p.smem_trsm, st>>>(A);
-        }
+        if (phase == 1)
+            k_trsm<T, true, 28><<<g, 256, p.smem_trsm, st>>>(A);
+        else
+            k_trsm<T, false, 28><<<g, 256, p.smem_trsm, st>>>(A);
     }
 }
 
