@@ -37,6 +37,7 @@ import numpy as np
 NL_CUBIC_GROUND = 1
 NL_CUBIC_DIFF = 2
 NL_VK_BEAM = 3
+NL_VDP = 4
 
 
 # -----------------------------------------------------------------------------
@@ -168,9 +169,11 @@ def fnl_and_tangent(model, q, qdot):
     difference spring, and the 2-node von Karman beam whose nonlinear
     internal force is the gradient of the axial-stretching energy
     EA/2 int (u' w'^2 + w'^4/4) dx with u linear and w Hermite cubic,
-    integrated exactly by 5-point Gauss-Legendre.  No element here depends on
-    qdot, so C_t = 0 (kept for the general interface).
-    Pinned by finite differences of f_nl (tests/test_oracle_newmark.py).
+    integrated exactly by 5-point Gauss-Legendre.  The self-excited damper
+    f = p0 (q^2 - 1) qdot (van der Pol) is the only element that depends on qdot
+    (C_t != 0); it is a test model for base frequencies that no forcing defines.
+    Pinned by finite differences of f_nl (tests/test_oracle_newmark.py,
+    tests/test_oracle_unknown_freq.py).
     """
     n = q.shape[0]
     f = np.zeros(n)
@@ -197,6 +200,12 @@ def fnl_and_tangent(model, q, qdot):
             Kt[j, j] += ke
             Kt[i, j] -= ke
             Kt[j, i] -= ke
+        elif t == NL_VDP:
+            i = int(dof[0])
+            c = p[0]
+            f[i] += c * (q[i] * q[i] - 1.0) * qdot[i]
+            Kt[i, i] += 2.0 * c * q[i] * qdot[i]
+            Ct[i, i] += c * (q[i] * q[i] - 1.0)
         elif t == NL_VK_BEAM:
             EA, L = p[0], p[1]
             loc = np.array([q[int(g)] if g >= 0 else 0.0 for g in dof[:6]])

@@ -30,6 +30,7 @@ import numpy as np
 NL_CUBIC_GROUND = 1
 NL_CUBIC_DIFF = 2
 NL_VK_BEAM = 3
+NL_VDP = 4             # self-excited (van der Pol) damper: f[d0] += p0 (q[d0]^2 - 1) qdot[d0]
 
 GOLDEN = (1.0 + math.sqrt(5.0)) / 2.0
 
@@ -487,6 +488,26 @@ def chain(n: int = 8, m: float = 1.0, k: float = 1e4, c: float = 1.0, k3: float 
         Fv[i, n // 2] = f
     return FEModel("chain_%d" % n, M, D, K, np.array(nl_type, np.int32), nl_dof, nl_p, Fv,
                    _first_mode(M, K))
+
+
+def van_der_pol(omega_n: float = 10.0, eps: float = 0.2, F: tuple = (1.0,)) -> FEModel:
+    """One self-excited oscillator q'' - eps omega_n (1 - q^2) q' + omega_n^2 q = sum F_i cos(w_i t).
+
+    Unit mass, no viscous damping, the textbook van der Pol damper as element type NL_VDP
+    (p0 = eps omega_n).  Its limit cycle (amplitude near 2, frequency near omega_n for small
+    eps) supplies a base frequency that no forcing defines: with e forcing components and
+    d > e base frequencies the remaining ones are unknowns of the torus (Sec. 3.2).
+    """
+    M = np.eye(1)
+    D = np.zeros((1, 1))
+    K = np.array([[omega_n * omega_n]])
+    nl_type = np.array([NL_VDP], np.int32)
+    nl_dof = np.full((1, 6), -1, np.int32)
+    nl_dof[0, 0] = 0
+    nl_p = np.zeros((1, 6))
+    nl_p[0, 0] = eps * omega_n
+    Fv = np.array(F, dtype=np.float64).reshape(-1, 1)
+    return FEModel("van_der_pol", M, D, K, nl_type, nl_dof, nl_p, Fv, omega_n)
 
 
 # ----------------------------------------------------------------------------
