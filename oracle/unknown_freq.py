@@ -22,7 +22,8 @@ shifted along phi_i is again a solution (Sec. 3.2.2).  Readings used here:
 
 Pinned by tests/test_oracle_unknown_freq.py: grad_i against finite differences of the
 trigonometric interpolant, dR(rho)/dw_i against finite differences of R(rho), dR/dw_i against
-finite differences of the residual, the closed-form discrete free oscillation (whose rotation
+finite differences of the residual (in w_i, and in w_1 with the unknown w_i held fixed), the
+closed-form discrete free oscillation (whose rotation
 number Newmark fixes exactly), the shift equivariance of the residual, and a brute-force
 long-time integration that stays on the solved torus with the solved frequency.
 """
@@ -82,6 +83,20 @@ def residual_unknown(model, S, H, S1, rho, Z0, omega1, unknown, tol=1e-10, maxit
     Z2 = rj.Z2pi.reshape(2 * prob.n, prob.U)
     cols = [(Z2 @ drotation_domega(prob.ktab, prob.rho, omega1, j).T).reshape(-1) for j in unknown]
     return prob, rj, cols
+
+
+def dR_domega1_unknown(prob, rj, omega1, unknown):
+    """dR/dw_1 of Eq. (23) when the frequencies w_{j+2}, j in ``unknown``, are held fixed (they
+    are unknowns of their own, Eq. Cont1) and the forced ratios are fixed (Eq. Cont2): the
+    integration term of ``residual_jacobian`` (rho fixed) plus the rotation term, whose angles
+    2 pi k~_l . rho move through rho_j = w_{j+2} / w_1, d rho_j / d w_1 = -rho_j / w_1 (the
+    Upsilon_1 case of Eq. 24 restricted to the unknown frequencies)."""
+    Z2 = rj.Z2pi.reshape(2 * prob.n, prob.U)
+    dR = np.zeros((prob.U, prob.U))
+    for j in unknown:
+        # dR(rho)/drho_j = w_1 dR(rho)/dw_{j+2}, times drho_j/dw_1 = -rho_j / w_1
+        dR -= prob.rho[j] * drotation_domega(prob.ktab, prob.rho, omega1, j)
+    return rj.dR_dw + (Z2 @ dR.T).reshape(-1)
 
 
 def newton_step_unknown(model, S, H, S1, rho, Z0, omega1, unknown, tol=1e-10, maxit=20):

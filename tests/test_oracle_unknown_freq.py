@@ -153,3 +153,26 @@ def test_vdp_torus_with_unknown_frequency_against_brute_force():
                                     sens=False, n_steps=k * S1)
         zk = UF.torus_point(prob, Z, [phi0 + 2.0 * np.pi * k * rho[0]])
         assert np.abs(tr.zT - zk).max() <= 3e-5 * np.abs(zk).max(), np.abs(tr.zT - zk).max()
+
+
+def test_dR_domega1_with_the_unknown_frequency_held_fixed_matches_fd():
+    """dR/dw_1 at fixed w_2 (unknown of its own): the integration term plus the rotation term of
+    rho_2 = w_2 / w_1 (Eq. 23, 24), against central differences of R in w_1 with w_2 fixed."""
+    m = I.van_der_pol(omega_n=WN, eps=0.2, F=(10.0,))
+    S, H, S1 = [8], [3], 48
+    rho = np.array([2.7])
+    w2 = rho[0] * W1
+    U = 2 * H[0] + 1
+    Z = np.random.default_rng(4).standard_normal(2 * U) * 0.3
+    prob, rj, cols = UF.residual_unknown(m, S, H, S1, rho, Z, W1, [0], tol=0, maxit=8)
+    an = UF.dR_domega1_unknown(prob, rj, W1, [0])
+    h = 1e-6 * W1
+    R = {}
+    for sgn in (1, -1):
+        w1 = W1 + sgn * h
+        R[sgn] = O.residual_jacobian(O.FSEProblem(m, S, H, S1, [w2 / w1]), Z, w1, want_jacobian=False, tol=0,
+                                     maxit=8).R
+    fd = (R[1] - R[-1]) / (2 * h)
+    np.testing.assert_allclose(an, fd, rtol=0, atol=1e-6 * np.abs(an).max())
+    # the rotation term matters: dropping it misses the derivative
+    assert np.abs(rj.dR_dw - fd).max() > 1e-3 * np.abs(fd).max()
