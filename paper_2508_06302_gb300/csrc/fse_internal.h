@@ -133,8 +133,8 @@ struct Params {
 struct fse_ctx {
     fse::Params p;
     fse::Dev d;
-    alignas(64) CUtensorMap tmX{};   // TMA maps of the tangent arrays X, V ([N][n][ld], boxes of
-    alignas(64) CUtensorMap tmV{};   // 32 rows x the right-hand-side kernel's column tile)
+    CUtensorMap tmX{};   // TMA maps of the tangent arrays X, V ([N][n][ld], boxes of 32 rows x the
+    CUtensorMap tmV{};   // right-hand-side kernel's column tile); the type carries its own alignment
     int device = 0;
     cudaStream_t stream = nullptr;   // state path + everything ordered
     cudaStream_t stream2 = nullptr;  // sensitivity kernels (overlap with the next state step)
