@@ -48,10 +48,15 @@ def parse():
                     help="small case: integrate only the first K Newmark steps of the period")
     ap.add_argument("--batch", action="store_true",
                     help="also time the 8-point shell batch (N = 32..64) as one graph against one by one")
-    ap.add_argument("--predictor", default="secant", choices=["secant", "mlp", "both"],
+    ap.add_argument("--predictor", default="mlp", choices=["secant", "mlp", "both"],
                     help="continuation predictor of --points (both: the two sweeps one after the other)")
-    ap.add_argument("--points", type=int, default=0,
-                    help="also time K converged continuation points (secant predictor, chord corrector)")
+    ap.add_argument("--points", type=int, default=-1,
+                    help="also time K converged continuation points (chord corrector, GMRES outer solve); "
+                         "default: 8 on one GPU, 0 under torchrun")
+    ap.add_argument("--fp64-points", type=int, default=-1,
+                    help="converged continuation points of the plain FP64 form timed for the points/s "
+                         "comparison (default: 1 when --points runs)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the GEMM peak measurements")
     return ap.parse_args()
 
 
@@ -258,9 +263,67 @@ def cpu_baseline(wl, seconds):
         if el >= seconds or done >= 200:
             break
         steps = max(1, min(20, int(steps * 2)))
-    return {"value": done / el, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": "%d traj-steps (with sensitivities) of one trajectory of %s in %.1f s"
-                      % (done, wl.name, el)}
+    threads = blas_threads()
+    return {"value": done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "host_cores": len(os.sched_getaffinity(0)),
+            "sample": "%d traj-steps (with sensitivities) of one trajectory of %s in %.1f s: the NumPy FP64 "
+                      "oracle as it stands, dense np.linalg.solve per Newton iteration and per tangent solve "
+                      "(no band, no parallelism over trajectories), BLAS threads %d"
+                      % (done, wl.name, el, threads)}
+
+
+def blas_threads():
+    """Threads of the BLAS the oracle's dense solves run on (threadpoolctl when present, else the
+    usual environment settings, else every host core: OpenBLAS's default)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [int(d.get("num_threads", 0)) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n and max(n) > 0:
+            return max(n)
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit() and int(v) > 0:
+            return int(v)
+    return len(os.sched_getaffinity(0))
+
+
+def gemm_peaks(torch):
+    """Measured dense-GEMM peaks of this GPU through cuBLAS (torch.matmul), best of several
+    launches timed with CUDA events: FP32 with TF32 off (the SIMT FMA pipes), TF32 tensor cores,
+    FP64 (DGEMM).  These are the denominators of the FP32 / TF32 / FP64 roofline fractions."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    out = {}
+    try:
+        for key, dtype, n, tf32, reps in (("fp32_simt_tflops", torch.float32, 8192, False, 5),
+                                         ("tf32_tflops", torch.float32, 8192, True, 8),
+                                         ("fp64_tflops", torch.float64, 4096, False, 3)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            g = torch.Generator(device="cuda")
+            g.manual_seed(0)
+            a = torch.randn(n, n, dtype=dtype, device="cuda", generator=g)
+            b = torch.randn(n, n, dtype=dtype, device="cuda", generator=g)
+            c = torch.empty(n, n, dtype=dtype, device="cuda")
+            for _ in range(2):
+                torch.matmul(a, b, out=c)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[key] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b, c
+        out["how"] = ("torch.matmul square GEMMs (FP32 8192^3 TF32 off and on, FP64 4096^3), 2 n^3 flops, "
+                      "best of 5/8/3 CUDA-event-timed launches")
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
 
 
 def batch_points(fse, device):
@@ -316,6 +379,7 @@ def continuation_points(fse, ctx, wl, K, predictor="secant", device=0):
     timed = pts[1:]
     tot_ms = sum(p["ms"] for p in timed)
     lin = ctx.linear_stats()
+    continuation_points.last = (omegas, Z, pts)
     return {"points": K, "predictor": predictor, "points_per_s": K / (tot_ms / 1e3) if tot_ms > 0 else None,
             "ms_per_point": [round(p["ms"], 1) for p in timed],
             "newton_iters": [p["newton_iters"] for p in timed],
@@ -329,6 +393,29 @@ def continuation_points(fse, ctx, wl, K, predictor="secant", device=0):
                             "status": pts[0]["status"]},
             "last_gmres": {"iters": lin[0], "rel_res": lin[1]},
             "omega1_over_wn1": [round(float(w / w_n1), 4) for w in omegas]}
+
+
+def fp64_points(fse, wl, omegas, Zconv, pts_mixed, K, device):
+    """The plain FP64 form (FP64 sensitivities, secant predictor, the same chord corrector and
+    GMRES outer solve) on K converged points of the same sweep: point j (j = 1..K) is corrected
+    from the mixed form's converged point j - 1, the prediction the mixed sweep also makes at
+    j = 1.  Its accepted tori are compared with the mixed form's (both accepted at
+    ||R|| <= 1e-10 ||Z||)."""
+    c64 = fse.Context.from_workload(wl, precision="fp64", device=device)
+    ms, its, diffs, sts = [], [], [], []
+    for j in range(1, K + 1):
+        Z, pts, rc = fse.fse_continue(c64, omegas[j:j + 1], Zconv[j - 1], rel_tol=1e-10, max_newton=40,
+                                      chord=True)
+        ms.append(pts[0]["ms"])
+        its.append(pts[0]["newton_iters"])
+        sts.append(pts[0]["status"])
+        diffs.append(float(np.linalg.norm(Z[0] - Zconv[j]) / np.linalg.norm(Zconv[j])))
+    c64.close()
+    tot = sum(ms)
+    return {"points": K, "predictor": "previous point (the mixed sweep's point-1 prediction)",
+            "points_per_s": K / (tot / 1e3), "ms_per_point": [round(x, 1) for x in ms], "newton_iters": its,
+            "status": sts, "rel_diff_vs_mixed_torus": diffs,
+            "mixed_same_start_ms": round(pts_mixed[1]["ms"], 1)}
 
 
 def half_bandwidth(model):
@@ -437,7 +524,7 @@ def main():
     # end-to-end through the host-pointer API (H2D of Z(0), D2H of R inside the timed region)
     Zh = initial_coeffs(wl)
     t0 = time.perf_counter()
-    n_e2e = max(1, args.steps // 2)
+    n_e2e = max(1, min(3, args.steps // 2))
     for _ in range(n_e2e):
         Rh, st_h, it_h, rc_h = ctx.residual_jacobian(Zh, w1, True)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
@@ -461,9 +548,11 @@ def main():
                 "sample": "%d of %d Newmark steps, all %d trajectories" % (args.fp64_steps, wl.S1, wl.N)}
         c64_short.close()
 
+    peaks_gemm = None if args.no_peaks else gemm_peaks(torch)
     peaks, src = measured_peaks()
-    # per-kernel rooflines of the sensitivity kernels (FP32 SIMT arithmetic or HBM, whichever
-    # bounds the kernel) from their event-timed average launch duration on the launching stream
+    # per-kernel rooflines of the sensitivity kernels (FP32 / FP64 SIMT arithmetic or HBM,
+    # whichever bounds the kernel) from their event-timed average launch duration on the
+    # launching stream
     names = ["state", "sens_rhs", "sens_fwd", "sens_bwd"]
     b = ctx.band
     n, N = m.n, wl.N
@@ -471,7 +560,10 @@ def main():
     work = step_work(m, N, b, 0, wb)
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     lanes = 128 if wb == 4 else 2            # FP32 / FP64 SIMT lanes per SM (FP64: 1/64 of FP32)
-    alu_peak = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_derived = n_sm * lanes * 2 * sm_mhz * 1e6 / 1e12
+    gkey = "fp32_simt_tflops" if wb == 4 else "fp64_tflops"
+    alu_peak = peaks_gemm[gkey] if peaks_gemm else alu_derived
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     kernels = {}
     for k_i, kname in enumerate(names):
@@ -501,14 +593,24 @@ def main():
                 "unit": kk["unit"], "frac": kk["frac"],
                 "traffic": recorded_traffic("k_" + kname, wl.name),
                 "peak_source": ("%s of %s (HBM copy)" % (hbm_peak, src)) if kk["bound"] == "hbm" else
-                ("152 SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (lanes, sm_mhz))}
+                (("measured cuBLAS %s GEMM (%s)" % ("FP32 TF32-off" if wb == 4 else "FP64", gkey)) if peaks_gemm
+                 else ("%d SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (n_sm, lanes, sm_mhz)))}
     batch = None
     if args.batch:
         batch = batch_points(fse, local)
     cont = None
-    if args.points > 0:
-        cont = {p: continuation_points(fse, ctx, wl, args.points, p, local)
-                for p in (["secant", "mlp"] if args.predictor == "both" else [args.predictor])}
+    n_points = args.points if args.points >= 0 else (8 if world == 1 else 0)
+    if n_points > 0:
+        cont = {}
+        for p in (["secant", "mlp"] if args.predictor == "both" else [args.predictor]):
+            cont[p] = continuation_points(fse, ctx, wl, n_points, p, local)
+        omegas, Zc, pts_c = continuation_points.last
+        k64 = args.fp64_points if args.fp64_points >= 0 else 1
+        if k64 > 0:
+            cont["fp64_plain"] = fp64_points(fse, wl, omegas, Zc, pts_c, min(k64, n_points), local)
+            best = max(v["points_per_s"] or 0.0 for k, v in cont.items() if k != "fp64_plain")
+            cont["vs_fp64_plain"] = best / cont["fp64_plain"]["points_per_s"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, args.cpu_seconds)
@@ -531,6 +633,8 @@ def main():
         # sensitivity kernels), join, DFT + residual
         "gpu_launches": args.steps * (4 * n_newmark + 6),
         "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "peaks_source": src,
+        "peaks_measured": peaks_gemm,
+        "alu_peak_derived_tflops": alu_derived,
     }
     if cont is not None:
         line["continuation"] = cont

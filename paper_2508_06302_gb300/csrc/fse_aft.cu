@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "fse_common.cuh"
@@ -377,10 +378,10 @@ void launch_dense_jac(fse_ctx* c, double* J) {
     const Params& p = c->p;
     const size_t m = (size_t)2 * p.n * p.U;
     if (p.prec == FSE_MIXED_FP32)
-        k_dense_jac<float><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+        k_dense_jac<float><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
             p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, J, m);
     else
-        k_dense_jac<double><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+        k_dense_jac<double><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
             p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, J, m);
 }
 
@@ -388,31 +389,33 @@ void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double 
     const Params& p = c->p;
     const size_t m = (size_t)2 * p.n * p.U;
     if (p.prec == FSE_MIXED_FP32)
-        k_dense_jac<float><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+        k_dense_jac<float><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
             p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, B, m + 1);
     else
-        k_dense_jac<double><<<nblocks(m * m, 256, 152 * 64), 256, 0, c->stream>>>(
+        k_dense_jac<double><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
             p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, B, m + 1);
     k_border<<<nblocks(m + 1, 256), 256, 0, c->stream>>>(m, Rw, tZ, tail, B);
 }
 
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m) {
-    int* flag = nullptr;
-    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return FSE_ENOMEM;
+    int* flag = c->d.flag + 1;   // zero-pivot flag: the context's second status word
     cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
     for (int k = 0; k < m; ++k) {
         k_lu_pivot<<<1, 1024, 0, c->stream>>>(A, bvec, c->piv, m, k, flag);
         if (k + 1 < m) {
             const size_t tot = (size_t)(m - k - 1) * (m - k);
-            k_lu_update<<<nblocks(tot, 256, 152 * 32), 256, 0, c->stream>>>(A, bvec, m, k);
+            k_lu_update<<<nblocks(tot, 256, 32), 256, 0, c->stream>>>(A, bvec, m, k);
             k_lu_mult<<<nblocks(m - k - 1, 256), 256, 0, c->stream>>>(A, m, k);
         }
     }
     k_back_subst<<<1, 1024, 0, c->stream>>>(A, bvec, m);
     int h = 0;
     cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
-    cudaFree(flag);
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("dense LU: ") + cudaGetErrorString(e);
+        return FSE_ECUDA;
+    }
     return h ? FSE_ENONPOS_PIVOT : FSE_OK;
 }
 
@@ -420,10 +423,18 @@ int lyapunov_run(fse_ctx* c, double w, int N_Ly, int h, double* sigma) {
     const Params& p = c->p;
     const int m = 2 * p.n;
     double *Q = nullptr, *A = nullptr, *acc = nullptr, *wts = nullptr;
-    if (cudaMalloc(&Q, sizeof(double) * m * h) != cudaSuccess) return FSE_ENOMEM;
-    cudaMalloc(&A, sizeof(double) * m * h);
-    cudaMalloc(&acc, sizeof(double) * h);
-    cudaMalloc(&wts, sizeof(double) * p.N);
+    cudaError_t ea = cudaMalloc(&Q, sizeof(double) * m * h);
+    if (ea == cudaSuccess) ea = cudaMalloc(&A, sizeof(double) * m * h);
+    if (ea == cudaSuccess) ea = cudaMalloc(&acc, sizeof(double) * h);
+    if (ea == cudaSuccess) ea = cudaMalloc(&wts, sizeof(double) * p.N);
+    if (ea != cudaSuccess) {
+        // nothing has been launched: free what was allocated and report before any kernel runs
+        cudaGetLastError();
+        for (double* q : {Q, A, acc, wts})
+            if (q) cudaFree(q);
+        c->err = std::string("Lyapunov scratch allocation failed: ") + cudaGetErrorString(ea);
+        return FSE_ENOMEM;
+    }
     std::vector<double> Q0((size_t)m * h, 0.0);
     for (int c2 = 0; c2 < h; ++c2) Q0[(size_t)c2 * h + c2] = 1.0;
     cudaMemcpyAsync(Q, Q0.data(), sizeof(double) * m * h, cudaMemcpyHostToDevice, c->stream);
@@ -450,7 +461,10 @@ int lyapunov_run(fse_ctx* c, double w, int N_Ly, int h, double* sigma) {
     cudaFree(A);
     cudaFree(acc);
     cudaFree(wts);
-    if (e != cudaSuccess) return FSE_ECUDA;
+    if (e != cudaSuccess) {
+        c->err = std::string("Lyapunov run: ") + cudaGetErrorString(e);
+        return FSE_ECUDA;
+    }
     const double T1 = 2.0 * M_PI / w;
     for (int j = 0; j < h; ++j) sigma[j] = hacc[j] / (N_Ly * T1);
     return FSE_OK;

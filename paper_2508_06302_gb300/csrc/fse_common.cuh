@@ -95,12 +95,16 @@ __device__ __forceinline__ double csr_row(const int* __restrict__ ptr, const int
     return acc;
 }
 
-// Block-wide max reduction of two values (blockDim.x multiple of 32, <= 1024).
+// max that propagates NaN from either argument (fmax drops it), so that a non-finite
+// value anywhere reaches the convergence test
+__device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+
+// Block-wide max reduction of two values (blockDim.x multiple of 32, <= 1024), NaN-propagating.
 __device__ __forceinline__ void block_max2(double& a, double& b) {
     __shared__ double ra[32], rb[32];
     for (int o = 16; o > 0; o >>= 1) {
-        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        a = nanmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = nanmax(b, __shfl_xor_sync(0xffffffffu, b, o));
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
@@ -113,8 +117,8 @@ __device__ __forceinline__ void block_max2(double& a, double& b) {
     a = 0.0;
     b = 0.0;
     for (int k = 0; k < nw; ++k) {
-        a = fmax(a, ra[k]);
-        b = fmax(b, rb[k]);
+        a = nanmax(a, ra[k]);
+        b = nanmax(b, rb[k]);
     }
 }
 
@@ -135,10 +139,12 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"((int)sizeof(T)));
 }
 
-static inline int nblocks(size_t total, int bs, int cap = 152 * 16) {
+// grid of a grid-stride loop: enough blocks for `total` items, at most per_sm blocks per SM
+static inline int nblocks(size_t total, int bs, int per_sm = 16) {
     size_t g = (total + bs - 1) / bs;
+    const size_t cap = (size_t)num_sms() * per_sm;
     if (g < 1) g = 1;
-    if (g > (size_t)cap) g = cap;
+    if (g > cap) g = cap;
     return (int)g;
 }
 

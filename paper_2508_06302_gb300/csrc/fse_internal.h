@@ -110,7 +110,8 @@ struct Dev {
     int* status = nullptr;   // N
     int* iters = nullptr;    // N
     int* nref = nullptr;     // N  in-loop refactorisations of the per-step Newton
-    int* flag = nullptr;     // error flag of the kernels' bounded waits (0 = fine)
+    int* flag = nullptr;     // 4 status words: [0] a bounded wait of a kernel gave up, [1] zero pivot of
+                             // the dense LU, [2] non-positive pivot of the M factor (0 = fine)
 };
 
 struct Params {
@@ -179,6 +180,23 @@ size_t trsm_smem(const Params& p);
 
 // TMA maps of X and V for the right-hand-side kernel (after the allocations)
 int make_tangent_maps(fse_ctx* c);
+
+// SM count of the current device (queried once per device and cached)
+inline int num_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int>& slot = cache[dev & 63];
+    int v = slot.load();
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
+        }
+        slot.store(v);
+    }
+    return v;
+}
 
 // launchers
 void ensure_constants();

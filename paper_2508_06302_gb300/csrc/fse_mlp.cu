@@ -449,8 +449,8 @@ int pod_build_dev(double* S, int nu, int m, int r, double* mean, double* basis, 
     if (e != cudaSuccess) {
         rc = FSE_ENOMEM;
     } else {
-        k_pod_mean<<<152, 256, 0, st>>>(m, nu, S, mean);
-        k_pod_center<<<152 * 4, 256, 0, st>>>(m, nu, S, mean);
+        k_pod_mean<<<fse::num_sms(), 256, 0, st>>>(m, nu, S, mean);
+        k_pod_center<<<fse::num_sms() * 4, 256, 0, st>>>(m, nu, S, mean);
         k_pod_gram<<<dim3(m, m), 256, 0, st>>>(m, nu, S, C);
         k_pod_jacobi<<<1, 256, 0, st>>>(m, C, V, 30);
         // eigenvalues (the diagonal) ordered by size on the host: index bookkeeping only

@@ -991,10 +991,10 @@ void launch_sens_init(fse_ctx* c, cudaStream_t st) {
     const Params& p = c->p;
     const size_t tot = (size_t)p.N * p.n * p.ld;
     if (p.prec == FSE_MIXED_FP32)
-        k_sens_init<float><<<nblocks(tot, 256, 152 * 64), 256, 0, st>>>(p.N, p.n, p.ld, (float*)c->d.X,
+        k_sens_init<float><<<nblocks(tot, 256, 64), 256, 0, st>>>(p.N, p.n, p.ld, (float*)c->d.X,
                                                                        (float*)c->d.V);
     else
-        k_sens_init<double><<<nblocks(tot, 256, 152 * 64), 256, 0, st>>>(p.N, p.n, p.ld, (double*)c->d.X,
+        k_sens_init<double><<<nblocks(tot, 256, 64), 256, 0, st>>>(p.N, p.n, p.ld, (double*)c->d.X,
                                                                         (double*)c->d.V);
 }
 

@@ -635,10 +635,16 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         if (tid < 32) warp_band_solve_fp64(A.LMc, A.LMr, A.LMinv, n, b, sb);
         __syncthreads();
         const double iw2 = 1.0 / (A.w * A.w);
+        double zmax = 0.0, amax = 0.0;
         for (int i = tid; i < n; i += nt) {
             sa[i] = sb[i] * iw2;
             A.a[off + i] = sa[i];
+            zmax = nanmax(zmax, nanmax(fabs(sq[i]), fabs(su[i])));
+            amax = nanmax(amax, fabs(sa[i]));
         }
+        block_max2(zmax, amax);
+        // a non-finite start point (from Z(0)) is reported as such, not as a failed factorisation
+        if (tid == 0 && (!isfinite(zmax) || !isfinite(amax))) s_stat = FSE_ENAN;
         __syncthreads();
     } else {
         const T* cLc = reinterpret_cast<const T*>(A.cLc) + foff;
@@ -669,8 +675,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             for (int i = tid; i < n; i += nt) {
                 const double v = sqn[i] - sr[i];
                 sqn[i] = v;
-                dmax = fmax(dmax, fabs(sr[i]));
-                qmax = fmax(qmax, fabs(v));
+                dmax = nanmax(dmax, fabs(sr[i]));
+                qmax = nanmax(qmax, fabs(v));
             }
             block_max2(dmax, qmax);
             if (!isfinite(dmax) || !isfinite(qmax)) {
@@ -786,15 +792,14 @@ int launch_factor_M(fse_ctx* c) {
     ensure_constants();
     const Params& p = c->p;
     const int nb = p.b + 1;
-    int* flag = nullptr;
-    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
+    int* flag = c->d.flag + 2;   // non-positive pivot of M: the context's third status word
+    cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
     const size_t smem = (size_t)(nb + 1 + FSE_CHOL_PF) * nb * sizeof(double);
     cudaFuncSetAttribute(k_factor_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_factor_M<<<1, 256, smem, c->stream>>>(p.n, p.b, c->d.Mb, c->d.LMc, c->d.LMr, c->d.LMinv, flag);
     int h = 0;
     cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaStreamSynchronize(c->stream);
-    cudaFree(flag);
     return h;
 }
 

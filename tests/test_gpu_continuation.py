@@ -23,8 +23,10 @@ def test_secant_continuation_matches_oracle():
     Z, pts, rc = fse.fse_continue(ctx, omegas, np.zeros(ctx.n_unknowns), rel_tol=1e-11, max_newton=8)
     assert rc == 0 and all(p["status"] == 0 for p in pts)
     prob = O.FSEProblem(m, [16], [7], 64, [I.GOLDEN])
-    for j in (0, 3, 5):
-        Zr, hist, ok = O.solve_torus(prob, Z[j], omegas[j], rel_tol=1e-12, tol=0, maxit=6)
+    # the oracle runs its own sweep (zeros, then its own previous solution): no GPU result seeds it
+    Zr = np.zeros(ctx.n_unknowns)
+    for j, w in enumerate(omegas):
+        Zr, hist, ok = O.solve_torus(prob, Zr, w, rel_tol=1e-13, tol=0, maxit=6)
         assert ok
         assert np.linalg.norm(Z[j] - Zr) <= 1e-9 * np.linalg.norm(Zr)
     # the secant predictor is better than the previous point once two points exist
