@@ -42,12 +42,16 @@ extern "C" {
 #define FSE_ECUDA (-6)         /* CUDA runtime error                         */
 #define FSE_ENOJAC (-7)        /* no Jacobian stored in the context yet      */
 
-/* Nonlinear element types of f_nl (Eq. 1).  None depends on qdot (C_t = 0). */
+/* Nonlinear element types of f_nl(q, qdot) (Eq. 1).  Only FSE_NL_VDP depends on qdot: its
+ * velocity tangent C_t = d f / d qdot enters the effective stiffness as w_1 (2/Delta) C_t and
+ * the sensitivity recurrence of App. E. */
 #define FSE_NL_CUBIC_GROUND 1  /* f[d0] += p0 q[d0]^3                          */
 #define FSE_NL_CUBIC_DIFF 2    /* s = q[d0]-q[d1]: f[d0] += p0 s^3, f[d1] -= p0 s^3 */
 #define FSE_NL_VK_BEAM 3       /* 2-node von Karman beam, dofs (u1,w1,th1,u2,w2,th2),
                                   p0 = EA, p1 = length; force = gradient of
                                   EA/2 int (u' w'^2 + w'^4/4) dx; dof -1 = clamped */
+#define FSE_NL_VDP 4           /* self-excited (van der Pol) damper:
+                                  f[d0] += p0 (q[d0]^2 - 1) qdot[d0]                */
 
 /* Precision of the sensitivity (monodromy) propagation.  The trajectory
  * state, the per-step Newton residual and test, the coupling residual and
@@ -100,6 +104,32 @@ typedef struct fse_ctx fse_ctx;
  * shared-memory vectors (about n > 3600 mixed, n > 2700 FP64, at b near 90).
  * On error *out is NULL.  device < 0 uses the current device. */
 int fse_setup(const fse_model* model, const fse_opts* opts, int device, fse_ctx** out);
+
+/* fse_setup for a trajectory shard: the context integrates only samples s_begin .. s_end - 1
+ * of the N-sample grid of opts (sample order of Eq. D1), with the grid's phases and the Gamma /
+ * Gamma^-1 entries of those samples (Eq. D2, D3, normalised by the whole N).  Trajectories are
+ * independent within an evaluation, so the shards of a torus can run on different GPUs; only the
+ * DFT sums over samples (Eq. 21, 22, 23) couple them.  On a shard context the residual, J v,
+ * dR/dw_1 and the hyper-time residual are completed by the reduction set with fse_set_reduce:
+ * the library forms this shard's partial sum, hands it to the reduction (which must return the
+ * sum over all shards in the same buffer) and subtracts Z0 / v afterwards.  Without a reduction
+ * those outputs are the partial sums (nothing subtracted).  Entry points that need every
+ * monodromy in one place (fse_jacobian_dense, the dense outer solve, fse_lyapunov*,
+ * fse_monodromy) return FSE_EINVAL on a shard.  Errors as fse_setup; FSE_EINVAL for a range
+ * outside [0, N). */
+int fse_setup_shard(const fse_model* model, const fse_opts* opts, int s_begin, int s_end, int device,
+                    fse_ctx** out);
+
+/* Reduction of partial DFT sums across shards: called synchronously (the context's stream has
+ * finished) with `count` doubles of this shard's partial sums in device memory at buf_dev; it
+ * must leave the sum over all shards (the same count, every shard's buffer in the same
+ * order) in buf_dev before returning, and return 0 (non-zero aborts the call with FSE_ECUDA).
+ * stream is the context's stream (a cudaStream_t). */
+typedef int (*fse_reduce_fn)(void* user, double* buf_dev, size_t count, void* stream);
+
+/* Set (or clear with fn = NULL) the reduction of a shard context.  FSE_EINVAL on a context that is
+ * not a shard. */
+int fse_set_reduce(fse_ctx* ctx, fse_reduce_fn fn, void* user);
 
 /* Wait for the context's work, free all its device memory and the handle.
  * NULL is ignored. */
@@ -186,10 +216,82 @@ int fse_newton_step(fse_ctx* ctx, double* Z0, double omega1, double* res_norm_ou
 #define FSE_LIN_GMRES 2
 int fse_set_linear_solver(fse_ctx* ctx, int kind, double rel_tol, int restart, int max_iters);
 
+/* Kernels of the banded tangent solves (App. E: the 2n+1 sensitivity columns of every
+ * trajectory through the factor L L^T of K_eff, forward L Y' = Y then backward L^T X = Y' with
+ * the Newmark update of V).  FSE_SOLVE_SIMT: blocked substitution on the FP32/FP64 FMA pipes.
+ * FSE_SOLVE_TC: the FP32 tangents on the TF32 tensor cores (tcgen05, accumulators in tensor
+ * memory) with both operands split into a TF32 high part and an FP32 remainder and three
+ * products per pair, which keeps FP32-level products; only for FSE_MIXED_FP32 contexts with
+ * half-bandwidth b <= 96.  FSE_SOLVE_AUTO (default): FSE_SOLVE_TC where it applies, else SIMT.
+ * Returns FSE_EINVAL for an unknown kind or FSE_SOLVE_TC where it does not apply. */
+#define FSE_SOLVE_AUTO 0
+#define FSE_SOLVE_SIMT 1
+#define FSE_SOLVE_TC 2
+int fse_set_tangent_solve(fse_ctx* ctx, int kind);
+
 /* Statistics of the last outer linear solve: Krylov iterations (0 for the
  * dense solve) and the relative residual ||J dZ + R|| / ||R|| it reached
  * (GMRES estimate; 0 for the dense solve). */
 int fse_linear_stats(const fse_ctx* ctx, int* iters, double* rel_res);
+
+/* ------------------------------------------------------------------------
+ * A priori unknown base frequencies (Sec. 3.2).  With e forcing components and d > e
+ * base frequencies, w_i for i > e is set by no forcing (a self-excited oscillation): it
+ * joins Z(0) as an unknown (Eq. Cont1), and the torus, which any shift along phi_i
+ * maps to another solution, is pinned by one phase condition per unknown (Eq. 18 with
+ * the gradient of Eq. 19).  w_1 stays fixed; w_i = rho_{i-1} w_1.
+ * ------------------------------------------------------------------------ */
+
+/* Set the frequency ratios rho_j = w_{j+1} / w_1 (d-1 doubles, host): rebuilds the rotation
+ * R(rho) of Eq. 14 and the tables that hold it, and drops the stored Jacobian.  Contexts in a
+ * graph batch must be re-batched after a change. */
+int fse_set_rho(fse_ctx* ctx, const double* rho);
+
+/* One Newton update of (Z(0), w_u) at fixed w_1 (Sec. 3.3 step 6 for Eq. Cont1):
+ * unknown (d-1 ints, host): unknown[j] != 0 makes w_{j+2} an unknown (FSE_EINVAL if forcing
+ * component j+1 moves with it, i.e. j + 1 < e); rho (d-1 doubles, host, in/out) holds the current
+ * ratios and receives the updated ones; Z0 (host, in/out) as for fse_newton_step.  The system is
+ *   [ J       dR/dw_u ] [dZ  ]     [R]
+ *   [ G_u^T   0       ] [dw_u] = - [0]
+ * with J of Eq. 22, dR/dw_u = (2 pi / w_1) (I (x) Upsilon_u) (I (x) R(rho)) Z(2 pi) (Eq. 23, 24,
+ * rotation term only: no trajectory moves with an unforced w_u) and the phase-condition rows
+ * G_u = (I (x) grad_u) Z0 (Eq. 18, 19), solved by dense LU (2 n U~ + u <= 16384) or GMRES on the
+ * bordered products, per fse_set_linear_solver.  res_norm_out (nullable): ||R(Z0_in)||_2.
+ * Returns as fse_newton_step. */
+int fse_newton_step_unknown(fse_ctx* ctx, double* Z0, double omega1, double* rho, const int* unknown,
+                            double* res_norm_out);
+
+/* ------------------------------------------------------------------------
+ * FSE-Shooting in the hyper-time domain (Sec. 3.4, Eq. FSES_T).  The unknowns are the
+ * start points zbar(0, phi~_s) of the N trajectories themselves, stored sample-major
+ * (N x 2n doubles, row s = [q; u] of trajectory s, the sample order of Eq. D1), instead of
+ * their Fourier coefficients.  The residual maps the end points back through the
+ * band-limited interpolant of the context's harmonics and rotates them:
+ *     R_T = (I_2n (x) Gamma R(rho) Gamma^-1) zbar(2 pi) - zbar(0),
+ * with Jacobian J_T = (I (x) Gamma R Gamma^-1) blockdiag(Phi_s) - I.  N may exceed U~ (more
+ * samples than coefficients); where zbar(0) = (I (x) Gamma) Z(0) the residual is
+ * (I (x) Gamma) R(Z(0)) of Eq. (16), so both forms share their tori.  The integration, the
+ * stored monodromies, the precision and the outer-solver settings are the context's.
+ * ------------------------------------------------------------------------ */
+
+/* One evaluation of R_T at (zbar0, w_1): zbar0 and RT_out host, N x 2n doubles;
+ * want_jacobian, traj_status and newton_iters as for fse_residual_jacobian (the stored
+ * monodromies also serve fse_jacobian_apply and friends).  Returns the worst trajectory
+ * status, FSE_ENOMEM if the form's buffers (4 N 2n + 2n U~ + N^2 doubles, allocated on first
+ * use and kept by the context) cannot be allocated. */
+int fse_residual_jacobian_hypertime(fse_ctx* ctx, const double* zbar0, double omega1, double* RT_out,
+                                    int want_jacobian, int* traj_status, int* newton_iters);
+
+/* J_T v for nvec vectors of N x 2n doubles (host, packed), from the monodromies of the last
+ * evaluation with want_jacobian (FSE_ENOJAC if there is none). */
+int fse_jacobian_apply_hypertime(fse_ctx* ctx, const double* v, double* Jv, int nvec);
+
+/* One Newton update of zbar0 (host, N x 2n, in/out) at fixed w_1: evaluates R_T and J_T,
+ * solves J_T dz = -R_T with the solver of fse_set_linear_solver (dense J_T and LU with partial
+ * pivoting up to 16384 unknowns, else GMRES on the products above) and adds dz.  res_norm_out
+ * (nullable) receives ||R_T(zbar0_in)||_2.  Returns the evaluation status, FSE_ENOCONV also when
+ * GMRES stops above its tolerance (the update is still applied). */
+int fse_newton_step_hypertime(fse_ctx* ctx, double* zbar0, double omega1, double* res_norm_out);
 
 /* First-order Lyapunov exponents (App. F) of the torus at (Z0, w_1), 1/s,
  * from the monodromy by-product: Psi_s = diag(I, w_1 I) Phi_s diag(I, I/w_1)

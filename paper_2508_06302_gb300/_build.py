@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libfse_gb300.so"
-SOURCES = ["fse_state.cu", "fse_sens.cu", "fse_aft.cu", "fse_mlp.cu", "fse_api.cu"]
+SOURCES = ["fse_state.cu", "fse_sens.cu", "fse_tc.cu", "fse_aft.cu", "fse_mlp.cu", "fse_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

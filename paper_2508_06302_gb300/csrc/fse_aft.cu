@@ -117,6 +117,35 @@ __global__ void k_dense_jac(int N, int n, int U, int P, const T* X, const T* V,
     }
 }
 
+// hyper-time form (Sec. 3.4, Eq. FSES_T): Pm = Gamma R(rho) Gamma^-1 (N x N), Pm[s][t] =
+// sum_c G[s][c] RG[c][t]
+__global__ void k_pmat(int N, int U, const double* __restrict__ G, const double* __restrict__ RG, double* Pm) {
+    const size_t total = (size_t)N * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = idx / N, t = idx % N;
+        double acc = 0.0;
+        for (int c = 0; c < U; ++c) acc += G[s * U + c] * RG[(size_t)c * N + t];
+        Pm[idx] = acc;
+    }
+}
+
+// dense Jacobian of Eq. FSES_T: J[(s,i),(t,j)] = Pm[s][t] Phi_t[i][j] - delta (unknowns sample-major)
+template <typename T>
+__global__ void k_dense_jac_ht(int N, int n, int P, const T* X, const T* V, const double* Pm, double* J) {
+    const int n2 = 2 * n;
+    const size_t m = (size_t)N * n2;
+    const size_t total = m * m;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = idx / m, col = idx % m;
+        const int s = (int)(row / n2), i = (int)(row % n2);
+        const int t = (int)(col / n2), j = (int)(col % n2);
+        const T* xr = (i < n ? X + ((size_t)t * n + i) * P : V + ((size_t)t * n + (i - n)) * P);
+        J[idx] = Pm[(size_t)s * N + t] * (double)xr[j] - (row == col ? 1.0 : 0.0);
+    }
+}
+
 // border of the pseudo-arclength system: column m = dR/dw_1, row m = (t_Z, tail)
 __global__ void k_border(size_t m, const double* __restrict__ Rw, const double* __restrict__ tZ, double tail,
                          double* B) {
@@ -128,6 +157,52 @@ __global__ void k_border(size_t m, const double* __restrict__ Rw, const double* 
             B[m * (m + 1) + m] = tail;
         }
     }
+}
+
+// Unknown base frequency w_{j+2} (Sec. 3.2, Eq. 18, 19, 23, 24), one harmonic row l of the table
+// (column j: k = k~_lj) acting on each (cos, sin) coefficient pair (a, b) of the 2n states:
+//   col = dR/dw_{j+2} = (2 pi / w_1) (I (x) Upsilon_j) (R + Z0), Upsilon: (a, b) -> (-k b, k a)
+//         ((I (x) R(rho)) Z(2 pi) = R + Z0; the trajectories do not move with an unforced w_i);
+//   row = (I (x) grad_j) Z0,                         grad:    (a, b) -> (k b, -k a)
+// (the phase condition of Eq. 18 on the Newton correction).  The constant coefficient gives 0.
+__global__ void k_unknown_border(size_t m, int U, int dm1, int j, const int* __restrict__ ktab, double scale,
+                                 const double* __restrict__ R, const double* __restrict__ Z0, double* col,
+                                 double* row) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < m; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = idx / U;
+        const int c = (int)(idx % U);
+        if (c == 0) {
+            col[idx] = 0.0;
+            row[idx] = 0.0;
+            continue;
+        }
+        const int l = (c - 1) >> 1;
+        const double k = (double)ktab[l * dm1 + j];
+        const size_t ci = i * U + 1 + 2 * l, si = ci + 1;
+        if (((c - 1) & 1) == 0) {   // cos coefficient
+            col[idx] = -scale * k * (R[si] + Z0[si]);
+            row[idx] = k * Z0[si];
+        } else {                    // sin coefficient
+            col[idx] = scale * k * (R[ci] + Z0[ci]);
+            row[idx] = -k * Z0[ci];
+        }
+    }
+}
+
+// border of a bordered m x m matrix with u extra columns / rows (lda = m + u): B[i][m + a] =
+// cols[a][i], B[m + a][i] = rows[a][i], B[m + a][m + b] = 0
+__global__ void k_border_multi(size_t m, int u, const double* __restrict__ cols, const double* __restrict__ rows,
+                               double* B) {
+    const size_t lda = m + u;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m + u; i += (size_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < u; ++a) {
+            if (i < m) {
+                B[i * lda + m + a] = cols[(size_t)a * m + i];
+                B[(m + a) * lda + i] = rows[(size_t)a * m + i];
+            } else {
+                B[(m + a) * lda + i] = 0.0;
+            }
+        }
 }
 
 // ----------------------------------------------------------------------------
@@ -385,6 +460,22 @@ void launch_dense_jac(fse_ctx* c, double* J) {
             p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, J, m);
 }
 
+void launch_pmat(fse_ctx* c, double* Pm) {
+    const Params& p = c->p;
+    k_pmat<<<nblocks((size_t)p.N * p.N, 256), 256, 0, c->stream>>>(p.N, p.U, c->d.G, c->d.RG, Pm);
+}
+
+void launch_dense_jac_ht(fse_ctx* c, const double* Pm, double* J) {
+    const Params& p = c->p;
+    const size_t m = (size_t)2 * p.n * p.N;
+    if (p.prec == FSE_MIXED_FP32)
+        k_dense_jac_ht<float><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.ld, (const float*)c->d.X, (const float*)c->d.V, Pm, J);
+    else
+        k_dense_jac_ht<double><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.ld, (const double*)c->d.X, (const double*)c->d.V, Pm, J);
+}
+
 void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double tail, double* B) {
     const Params& p = c->p;
     const size_t m = (size_t)2 * p.n * p.U;
@@ -395,6 +486,26 @@ void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double 
         k_dense_jac<double><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
             p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, B, m + 1);
     k_border<<<nblocks(m + 1, 256), 256, 0, c->stream>>>(m, Rw, tZ, tail, B);
+}
+
+void launch_unknown_border(fse_ctx* c, int j, double w, const double* R, const double* Z0, double* col,
+                           double* row) {
+    const Params& p = c->p;
+    const size_t m = (size_t)2 * p.n * p.U;
+    k_unknown_border<<<nblocks(m, 256), 256, 0, c->stream>>>(m, p.U, p.d - 1, j, c->d.ktab, 2.0 * M_PI / w, R, Z0,
+                                                             col, row);
+}
+
+void launch_dense_jac_bordered(fse_ctx* c, int u, const double* cols, const double* rows, double* B) {
+    const Params& p = c->p;
+    const size_t m = (size_t)2 * p.n * p.U;
+    if (p.prec == FSE_MIXED_FP32)
+        k_dense_jac<float><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.U, p.ld, (const float*)c->d.X, (const float*)c->d.V, c->d.RG, c->d.G, B, m + u);
+    else
+        k_dense_jac<double><<<nblocks(m * m, 256, 64), 256, 0, c->stream>>>(
+            p.N, p.n, p.U, p.ld, (const double*)c->d.X, (const double*)c->d.V, c->d.RG, c->d.G, B, m + u);
+    k_border_multi<<<nblocks(m + u, 256), 256, 0, c->stream>>>(m, u, cols, rows, B);
 }
 
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m) {

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -111,16 +112,36 @@ static RowGroups group_rows(int n, const std::vector<int>& cptr, const std::vect
 // bytes of one group record: the ring slot (int, padded to 8 bytes), then 2R values
 static int group_record_bytes(int R, size_t tsz) { return (int)((8 + 2 * R * tsz + 15) / 16 * 16); }
 
+// cos and sin of the rotation angles 2 pi k~_l . rho of Eq. (14), l < L, for the context's rho
+static void rotation_tables(const fse_ctx* c, std::vector<double>& rc, std::vector<double>& rs) {
+    const int L = c->p.L, dm1 = c->p.d - 1;
+    rc.assign(std::max(L, 1), 0.0);
+    rs.assign(std::max(L, 1), 0.0);
+    for (int l = 0; l < L; ++l) {
+        double th = 0.0;
+        for (int j = 0; j < dm1; ++j) th += (double)c->ktab_host[(size_t)l * dm1 + j] * c->rho[j];
+        th *= 2.0 * M_PI;
+        rc[l] = cos(th);
+        rs[l] = sin(th);
+    }
+}
+
+// dofs of a nonlinear element type (FSE_NL_*)
+static int host_elem_ndof(int type) {
+    return (type == FSE_NL_CUBIC_GROUND || type == FSE_NL_VDP) ? 1 : (type == FSE_NL_CUBIC_DIFF ? 2 : 6);
+}
+
 static void free_ctx(fse_ctx* c) {
     if (!c) return;
     void* ptrs[] = {c->d.Mb, c->d.F, c->d.el_type, c->d.el_dof, c->d.el_p, c->d.col_off,
                     c->d.cs_ptr, c->d.cs_col, c->d.kt_slot, c->d.g_pass, c->d.g_info, c->d.g_rr, c->d.g_map, c->d.g_slot,
                     c->d.g_rec, c->d.cs_m, c->d.cs_d, c->d.cs_k, c->d.cs_s, c->d.cs_A,
                     c->d.cs_B, c->d.kt_ptr, c->d.kt_col, c->d.kt_soff, c->d.kt_src, c->d.ke,
-                    c->d.kt_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
+                    c->d.kt_val, c->d.ce, c->d.ct_val, c->d.romega, c->d.phis, c->d.G, c->d.Gi, c->d.RG, c->d.rc, c->d.rs,
                     c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
-                    c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.Rf, c->d.Rb, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
-                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv, c->kry, c->kdot};
+                    c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.Rf, c->d.Rb, c->d.Tf, c->d.Tb, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
+                    c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv, c->kry, c->kdot,
+                    c->ht, c->unk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -133,7 +154,23 @@ static void free_ctx(fse_ctx* c) {
     delete c;
 }
 
+static int setup_impl(const fse_model* m, const fse_opts* o, long long s_begin, long long s_end, int device,
+                      fse_ctx** out);
+
 extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_ctx** out) {
+    return setup_impl(m, o, 0, -1, device, out);
+}
+
+extern "C" int fse_setup_shard(const fse_model* m, const fse_opts* o, int s_begin, int s_end, int device,
+                               fse_ctx** out) {
+    if (out) *out = nullptr;
+    if (s_begin < 0 || s_end <= s_begin) return set_err(nullptr, FSE_EINVAL, "need 0 <= s_begin < s_end");
+    return setup_impl(m, o, s_begin, s_end, device, out);
+}
+
+// s_end < 0: every trajectory (s_begin = 0)
+static int setup_impl(const fse_model* m, const fse_opts* o, long long s_begin, long long s_end, int device,
+                      fse_ctx** out) {
     if (!out) return set_err(nullptr, FSE_EINVAL, "out is NULL");
     *out = nullptr;
     if (!m || !o) return set_err(nullptr, FSE_EINVAL, "model or opts is NULL");
@@ -157,6 +194,14 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         U *= 2 * H[j] + 1;
     }
     if (N > 65535 || U > 65535) return set_err(nullptr, FSE_EINVAL, "N or U too large");
+    // trajectory shard [s_begin, s_end) of the N-sample grid (the whole grid by default)
+    const long long Nglob = N;
+    if (s_end < 0) {
+        s_begin = 0;
+        s_end = Nglob;
+    }
+    if (s_end > Nglob) return set_err(nullptr, FSE_EINVAL, "shard beyond the trajectory grid");
+    N = s_end - s_begin;
     for (int j = 0; j < o->d - 1; ++j)
         if (!std::isfinite(o->rho[j])) return set_err(nullptr, FSE_EINVAL, "rho not finite");
     // half-bandwidth from exact zeros and element spans
@@ -168,8 +213,8 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         }
     for (int e = 0; e < m->n_nl; ++e) {
         const fse_nl_elem& el = m->nl[e];
-        if (el.type < 1 || el.type > 3) return set_err(nullptr, FSE_EINVAL, "unknown element type");
-        const int nd = el.type == 1 ? 1 : (el.type == 2 ? 2 : 6);
+        if (el.type < 1 || el.type > 4) return set_err(nullptr, FSE_EINVAL, "unknown element type");
+        const int nd = host_elem_ndof(el.type);
         for (int a = 0; a < nd; ++a) {
             if (el.dof[a] >= n || el.dof[a] < -1) return set_err(nullptr, FSE_EINVAL, "element dof out of range");
             if (el.type != 3 && el.dof[a] < 0) return set_err(nullptr, FSE_EINVAL, "spring dof must be >= 0");
@@ -186,6 +231,9 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.d = o->d;
     p.e = m->e;
     p.N = (int)N;
+    p.N_glob = (int)Nglob;
+    p.s0 = (int)s_begin;
+    p.shard = N != Nglob;
     p.U = (int)U;
     p.L = (int)(U - 1) / 2;
     p.S1 = o->S1;
@@ -194,6 +242,8 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.prec = o->precision;
     p.tol = o->newton_tol;
     p.n_el = m->n_nl;
+    for (int e = 0; e < m->n_nl; ++e)
+        if (m->nl[e].type == FSE_NL_VDP) p.has_vel = true;
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
     const int nb = b + 1;
     for (int j = 0; j < o->d - 1; ++j) c->rho.push_back(o->rho[j]);
@@ -230,7 +280,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     // sample grid (Eq. D1): phi_2 fastest
     std::vector<double> phis((size_t)N * dm1);
     for (long long s = 0; s < N; ++s) {
-        long long rem = s;
+        long long rem = s_begin + s;
         for (int j = 0; j < dm1; ++j) {
             const long long ij = rem % S[j];
             rem /= S[j];
@@ -238,14 +288,8 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
         }
     }
     // rotation angles 2 pi k~_l . rho (Eq. 14)
-    std::vector<double> rcv(std::max(p.L, 1)), rsv(std::max(p.L, 1));
-    for (int l = 0; l < p.L; ++l) {
-        double th = 0.0;
-        for (int j = 0; j < dm1; ++j) th += (double)rows[l][j] * o->rho[j];
-        th *= 2.0 * M_PI;
-        rcv[l] = cos(th);
-        rsv[l] = sin(th);
-    }
+    std::vector<double> rcv, rsv;
+    rotation_tables(c, rcv, rsv);
     // diagonal-major full band of M (for its factor) and the CSR of the union pattern of M, D, K
     const int fb = 2 * b + 1;
     std::vector<double> Mb((size_t)fb * n, 0.0);
@@ -271,7 +315,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     int ncol = 0;
     for (int e = 0; e < m->n_nl; ++e) {
         const fse_nl_elem& el = m->nl[e];
-        const int nd = el.type == 1 ? 1 : (el.type == 2 ? 2 : 6);
+        const int nd = host_elem_ndof(el.type);
         uint64_t mask = 0;
         for (int a = 0; a < nd; ++a)
             if (el.dof[a] >= 0) mask |= used[el.dof[a]];
@@ -332,6 +376,8 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     p.nnz_kt = (int)kcol.size();
     p.nblk = (n + FSE_BLK - 1) / FSE_BLK;
     p.RECE = ((b + 3) & ~3) * FSE_BLK + FSE_BLK * FSE_BLK;
+    p.ND = (b + FSE_BLK - 1) / FSE_BLK;
+    p.tc_ok = p.prec == FSE_MIXED_FP32 && b <= 96;
     p.ld = (p.P + 3) & ~3;
     // row groups: R chosen by the shared-memory wavefronts per 64-column pass of an entry
     // (4 for the X and V elements, RB / 16 for the broadcast record)
@@ -466,6 +512,10 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     A(&c->d.kt_src, (size_t)std::max<size_t>(1, ksrc.size()) * 4);
     A(&c->d.ke, (size_t)N * std::max(1, m->n_nl) * 36 * 8);
     A(&c->d.kt_val, FSE_NBUF_KT * ktsz);
+    if (p.has_vel) {
+        A(&c->d.ce, (size_t)N * std::max(1, m->n_nl) * 36 * 8);
+        A(&c->d.ct_val, FSE_NBUF_KT * ktsz);
+    }
     A(&c->d.romega, (size_t)2 * Nn * tsz);
     A(&c->d.phis, (size_t)N * dm1 * 8);
     A(&c->d.G, (size_t)N * U * 8);
@@ -489,6 +539,11 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     const size_t rsz = (size_t)N * p.nblk * p.RECE * tsz;
     A(&c->d.Rf, FSE_NBUF_F * rsz);
     A(&c->d.Rb, FSE_NBUF_F * rsz);
+    if (p.tc_ok) {
+        const size_t tcsz = (size_t)N * (p.nblk + 1) * 8 * FSE_BLK * FSE_BLK * 4;
+        A(&c->d.Tf, tcsz);
+        A(&c->d.Tb, tcsz);
+    }
     A(&c->d.X, sensz);
     A(&c->d.V, sensz);
     A(&c->d.Y, sensz);
@@ -525,6 +580,7 @@ extern "C" int fse_setup(const fse_model* m, const fse_opts* o, int device, fse_
     cudaMemcpyAsync(c->d.g_slot, gslot.data(), gslot.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.kt_slot, kslot.data(), kslot.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(c->d.kt_val, 0, FSE_NBUF_KT * ktsz, st);
+    if (p.has_vel) cudaMemsetAsync(c->d.ct_val, 0, FSE_NBUF_KT * ktsz, st);
     cudaMemcpyAsync(c->d.cs_m, cm.data(), cm.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_d, cd.data(), cd.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_k, ck.data(), ck.size() * 8, cudaMemcpyHostToDevice, st);
@@ -591,8 +647,45 @@ extern "C" int fse_harmonics(const fse_ctx* c, int* kt) {
     return FSE_OK;
 }
 
-// the whole evaluation, asynchronous on the context stream
-static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, int sens) {
+// Trajectory shards: the partial DFT sums in buf (count doubles) become the whole torus's sums
+// through the context's reduction, then sub (nullable) is subtracted.  Without a reduction the
+// partial sums are the result.  Synchronous (the reduction runs on the host).
+static int shard_complete(fse_ctx* c, double* buf, size_t count, const double* sub) {
+    if (!c->p.shard || !c->reduce) return FSE_OK;
+    int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "shard partial sums");
+    if (rc) return rc;
+    if (c->reduce(c->reduce_user, buf, count, (void*)c->stream) != 0) {
+        c->reduce_failed = true;
+        return set_err(c, FSE_ECUDA, "shard reduction failed");
+    }
+    if (sub) fse::vec_axpby(c, count, -1.0, sub, 1.0, buf);
+    return FSE_OK;
+}
+
+// out = (I (x) R Gamma^-1) zb - sub, or on a shard the completed sum minus sub
+static int dft_sub(fse_ctx* c, const double* zb, const double* sub, double* out) {
+    const size_t nu = (size_t)2 * c->p.n * c->p.U;
+    fse::launch_dft_residual(c, zb, sub, out, (sub && !c->p.shard) ? 1 : 0);
+    return shard_complete(c, out, nu, sub);
+}
+
+// R_T = Gamma R(rho) Gamma^-1 zbar(2 pi) - zbar(0) of Eq. FSES_T from the end points in d.zb:
+// DFT + rotation into the coefficient scratch, i-DFT back to the samples, minus the start points
+static int hypertime_residual(fse_ctx* c, const double* zb0_dev, double* RT_dev) {
+    const Params& p = c->p;
+    double* coef = c->ht + (size_t)4 * p.N * 2 * p.n;
+    const int rc = dft_sub(c, c->d.zb, nullptr, coef);
+    if (rc) return rc;
+    fse::launch_idft(c, coef, RT_dev);
+    fse::vec_axpby(c, (size_t)p.N * 2 * p.n, -1.0, zb0_dev, 1.0, RT_dev);
+    return FSE_OK;
+}
+
+// the whole evaluation, asynchronous on the context stream.  The trajectories start from the
+// i-DFT of the coefficients Z0_dev (Eq. 20), or, when zb0_dev is given, from the start points
+// zbar(0) themselves (the hyper-time form of Sec. 3.4, N x 2n): then R_dev receives R_T.
+static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, int sens,
+                    const double* zb0_dev = nullptr) {
     if (!(w > 0.0) || !std::isfinite(w)) return set_err(c, FSE_EINVAL, "omega1 must be positive and finite");
     cudaSetDevice(c->device);
     const Params& p = c->p;
@@ -617,7 +710,10 @@ static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, i
     };
     cudaStream_t s1 = c->stream, s2 = c->stream2;
     cudaEventRecord(c->ev[0], s1);
-    fse::launch_idft(c, Z0_dev, c->d.zb);
+    if (zb0_dev)
+        cudaMemcpyAsync(c->d.zb, zb0_dev, (size_t)p.N * 2 * p.n * 8, cudaMemcpyDeviceToDevice, s1);
+    else
+        fse::launch_idft(c, Z0_dev, c->d.zb);
     fse::launch_init_state(c, w);
     if (sens) {
         cudaEventRecord(c->ev[2], s1);
@@ -647,7 +743,8 @@ static int run_eval(fse_ctx* c, const double* Z0_dev, double w, double* R_dev, i
     c->prof_sens = sens != 0;
     c->prof_steps = steps;
     fse::launch_collect_end(c);
-    fse::launch_dft_residual(c, c->d.zb, Z0_dev, R_dev, 1);
+    const int rcd = zb0_dev ? hypertime_residual(c, zb0_dev, R_dev) : dft_sub(c, c->d.zb, Z0_dev, R_dev);
+    if (rcd) return rcd;
     if (sens) cudaStreamWaitEvent(s1, c->ev_sens[steps - 1], 0);
     cudaEventRecord(c->ev[1], s1);
     c->have_jac = sens != 0;
@@ -745,7 +842,8 @@ extern "C" int fse_jacobian_apply(fse_ctx* c, const double* v, double* Jv, int n
         cudaMemcpyAsync(c->d.vec, v + k * nu, nu * 8, cudaMemcpyHostToDevice, c->stream);
         fse::launch_idft(c, c->d.vec, c->d.zb);
         fse::launch_phi_apply(c, c->d.zb, c->d.yb);
-        fse::launch_dft_residual(c, c->d.yb, c->d.vec, c->d.vec2, 1);
+        const int rc = dft_sub(c, c->d.yb, c->d.vec, c->d.vec2);
+        if (rc) return rc;
         cudaMemcpyAsync(Jv + k * nu, c->d.vec2, nu * 8, cudaMemcpyDeviceToHost, c->stream);
     }
     return cuda_check(c, cudaStreamSynchronize(c->stream), "jacobian_apply");
@@ -757,7 +855,8 @@ extern "C" int fse_jacobian_domega(fse_ctx* c, double* out) {
     cudaSetDevice(c->device);
     const size_t nu = (size_t)2 * c->p.n * c->p.U;
     fse::launch_domega(c, c->d.yb);
-    fse::launch_dft_residual(c, c->d.yb, nullptr, c->d.vec2, 0);
+    const int rc = dft_sub(c, c->d.yb, nullptr, c->d.vec2);
+    if (rc) return rc;
     cudaMemcpyAsync(out, c->d.vec2, nu * 8, cudaMemcpyDeviceToHost, c->stream);
     return cuda_check(c, cudaStreamSynchronize(c->stream), "jacobian_domega");
 }
@@ -777,6 +876,7 @@ static int ensure_dense(fse_ctx* c, size_t m) {
 }
 
 extern "C" int fse_jacobian_dense(fse_ctx* c, double* J) {
+    if (c && c->p.shard) return set_err(c, FSE_EINVAL, "not available on a trajectory shard");
     if (!c || !J) return FSE_EINVAL;
     if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored");
     const size_t m = (size_t)2 * c->p.n * c->p.U;
@@ -855,18 +955,18 @@ static int eval_at_iterate(fse_ctx* c, double w, int sens, double* rn, double* z
 }
 
 // w = J v with the stored monodromies (Eq. 22): i-DFT, blockdiag(Phi_s), DFT + rotation, minus v
+// (a failed shard reduction is recorded in c->reduce_failed for the caller)
 static void jac_apply_dev(fse_ctx* c, const double* v, double* w) {
     fse::launch_idft(c, v, c->d.zb);
     fse::launch_phi_apply(c, c->d.zb, c->d.yb);
-    fse::launch_dft_residual(c, c->d.yb, v, w, 1);
+    dft_sub(c, c->d.yb, v, w);
 }
 
 // Restarted GMRES(m) on J x = b (b, x on the device, x0 = 0), FP64, classical Gram-Schmidt with
 // one re-orthogonalisation pass; the small Hessenberg least-squares problem is reduced by
 // Givens rotations on the host.  Returns FSE_OK, or FSE_ENOCONV when it stops above rtol.
-static int gmres_dev(fse_ctx* c, const double* b, double* x, double rtol, int m, int maxit, int* iters_out,
-                     double* relres_out) {
-    const size_t n = (size_t)2 * c->p.n * c->p.U;
+static int gmres_dev(fse_ctx* c, size_t n, const std::function<void(const double*, double*)>& Av, const double* b,
+                     double* x, double rtol, int m, int maxit, int* iters_out, double* relres_out) {
     if ((size_t)(m + 1) * n > c->kry_cap) {
         if (c->kry) cudaFree(c->kry);
         if (c->kdot) cudaFree(c->kdot);
@@ -907,7 +1007,7 @@ static int gmres_dev(fse_ctx* c, const double* b, double* x, double rtol, int m,
         if (first) {
             cudaMemcpyAsync(v0, b, n * 8, cudaMemcpyDeviceToDevice, c->stream);
         } else {
-            jac_apply_dev(c, x, v0);
+            Av(x, v0);
             fse::vec_axpby(c, n, 1.0, b, -1.0, v0);
         }
         first = false;
@@ -922,7 +1022,7 @@ static int gmres_dev(fse_ctx* c, const double* b, double* x, double rtol, int m,
         int k = 0;
         for (; k < m && it < maxit; ++k) {
             double* w = Vb + (size_t)(k + 1) * n;
-            jac_apply_dev(c, Vb + (size_t)k * n, w);
+            Av(Vb + (size_t)k * n, w);
             ++it;
             // two passes of classical Gram-Schmidt against v_0..v_k
             std::fill(hcol.begin(), hcol.end(), 0.0);
@@ -984,7 +1084,10 @@ static int gmres_dev(fse_ctx* c, const double* b, double* x, double rtol, int m,
 // Returns FSE_OK, FSE_ENOCONV (GMRES stopped above its tolerance; the update is applied) or an error.
 static int newton_solve_update(fse_ctx* c) {
     const size_t m = (size_t)2 * c->p.n * c->p.U;
-    const bool dense = c->lin_kind == FSE_LIN_DENSE || (c->lin_kind == FSE_LIN_AUTO && m <= 16384);
+    const bool dense = !c->p.shard && (c->lin_kind == FSE_LIN_DENSE || (c->lin_kind == FSE_LIN_AUTO && m <= 16384));
+    if (c->p.shard && c->lin_kind == FSE_LIN_DENSE)
+        return set_err(c, FSE_EINVAL, "a trajectory shard has no dense Jacobian: use GMRES");
+    c->reduce_failed = false;
     c->lin_iters = 0;
     c->lin_relres = 0.0;
     if (dense) {
@@ -1001,9 +1104,12 @@ static int newton_solve_update(fse_ctx* c) {
     fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, c->d.vec2);          // rhs = -R
     int it = 0;
     double rel = 0.0;
-    const int rc = gmres_dev(c, c->d.vec2, c->d.vec, c->lin_rtol, c->lin_restart, c->lin_maxit, &it, &rel);
+    const int rc = gmres_dev(
+        c, m, [c](const double* v, double* w) { jac_apply_dev(c, v, w); }, c->d.vec2, c->d.vec, c->lin_rtol,
+        c->lin_restart, c->lin_maxit, &it, &rel);
     c->lin_iters = it;
     c->lin_relres = rel;
+    if (c->reduce_failed) return set_err(c, FSE_ECUDA, "shard reduction failed");
     if (rc != FSE_OK && rc != FSE_ENOCONV) return rc;
     fse::vec_axpby(c, m, 1.0, c->d.vec, 1.0, c->d.Z0);           // Z0 += dZ
     const int rc2 = cuda_check(c, cudaStreamSynchronize(c->stream), "newton update");
@@ -1047,7 +1153,236 @@ extern "C" int fse_newton_step(fse_ctx* c, double* Z0, double w, double* res_nor
     return st != FSE_OK ? st : lin;
 }
 
+// ----------------------------------------------------------------------------
+// FSE-Shooting in the hyper-time domain (Sec. 3.4, Eq. FSES_T): the start points zbar(0, phi~_s)
+// are the unknowns; R_T = (I (x) Gamma R Gamma^-1) zbar(2 pi) - zbar(0), J_T = (I (x) Gamma R
+// Gamma^-1) blockdiag(Phi_s) - I.  Vectors are sample-major, N x 2n.
+// ----------------------------------------------------------------------------
+
+// device buffers of the hyper-time form, allocated on first use: start points, residual, two
+// scratch vectors (N x 2n each), a coefficient vector (2n U~) and Gamma R Gamma^-1 (N x N)
+static int ensure_hypertime(fse_ctx* c) {
+    if (c->ht) return FSE_OK;
+    const Params& p = c->p;
+    const size_t m = (size_t)p.N * 2 * p.n;
+    const size_t tot = 4 * m + (size_t)2 * p.n * p.U + (size_t)p.N * p.N;
+    cudaError_t e = cudaMalloc(&c->ht, tot * 8);
+    if (e != cudaSuccess) {
+        c->ht = nullptr;
+        return cuda_check(c, e, "hyper-time buffers");
+    }
+    c->ht_pm = false;
+    return FSE_OK;
+}
+
+// w = J_T v: blockdiag(Phi_s) v, DFT + rotation, i-DFT, minus v
+static void jac_apply_ht_dev(fse_ctx* c, const double* v, double* w) {
+    const Params& p = c->p;
+    const size_t m = (size_t)p.N * 2 * p.n;
+    double* coef = c->ht + 4 * m;
+    fse::launch_phi_apply(c, v, c->d.yb);
+    dft_sub(c, c->d.yb, nullptr, coef);
+    fse::launch_idft(c, coef, w);
+    fse::vec_axpby(c, m, -1.0, v, 1.0, w);
+}
+
+extern "C" int fse_residual_jacobian_hypertime(fse_ctx* c, const double* zbar0, double w, double* RT_out,
+                                               int want_jacobian, int* ts, int* it) {
+    if (!c || !zbar0 || !RT_out) return FSE_EINVAL;
+    cudaSetDevice(c->device);
+    int rc = ensure_hypertime(c);
+    if (rc) return rc;
+    const size_t m = (size_t)c->p.N * 2 * c->p.n;
+    cudaMemcpyAsync(c->ht, zbar0, m * 8, cudaMemcpyHostToDevice, c->stream);
+    rc = run_eval(c, nullptr, w, c->ht + m, want_jacobian, c->ht);
+    if (rc) return rc;
+    cudaMemcpyAsync(RT_out, c->ht + m, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    return collect_status(c, ts, it);
+}
+
+extern "C" int fse_jacobian_apply_hypertime(fse_ctx* c, const double* v, double* Jv, int nvec) {
+    if (!c || !v || !Jv || nvec < 0) return FSE_EINVAL;
+    if (!c->have_jac) return set_err(c, FSE_ENOJAC, "no Jacobian stored: evaluate with want_jacobian=1 first");
+    cudaSetDevice(c->device);
+    int rc = ensure_hypertime(c);
+    if (rc) return rc;
+    const size_t m = (size_t)c->p.N * 2 * c->p.n;
+    double* a = c->ht + 2 * m;
+    double* b = c->ht + 3 * m;
+    for (int k = 0; k < nvec; ++k) {
+        cudaMemcpyAsync(a, v + k * m, m * 8, cudaMemcpyHostToDevice, c->stream);
+        jac_apply_ht_dev(c, a, b);
+        cudaMemcpyAsync(Jv + k * m, b, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "jacobian_apply_hypertime");
+}
+
+extern "C" int fse_newton_step_hypertime(fse_ctx* c, double* zbar0, double w, double* res_norm) {
+    if (!c || !zbar0) return FSE_EINVAL;
+    cudaSetDevice(c->device);
+    int rc = ensure_hypertime(c);
+    if (rc) return rc;
+    const Params& p = c->p;
+    const size_t m = (size_t)p.N * 2 * p.n;
+    double* z0 = c->ht;
+    double* rt = c->ht + m;
+    double* a = c->ht + 2 * m;
+    double* b = c->ht + 3 * m;
+    double* Pm = c->ht + 4 * m + (size_t)2 * p.n * p.U;
+    cudaMemcpyAsync(z0, zbar0, m * 8, cudaMemcpyHostToDevice, c->stream);
+    rc = run_eval(c, nullptr, w, rt, 1, z0);
+    if (rc) return rc;
+    const int st = collect_status(c, nullptr, nullptr);
+    if (st < 0 && st != FSE_ENOCONV) return st;
+    fse::vec_norms2(c, m, rt, nullptr, c->d.vec2);
+    double h2[2];
+    cudaMemcpyAsync(h2, c->d.vec2, 16, cudaMemcpyDeviceToHost, c->stream);
+    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "hyper-time residual norm");
+    if (rc) return rc;
+    if (res_norm) *res_norm = std::sqrt(h2[0]);
+    fse::vec_axpby(c, m, -1.0, rt, 0.0, b);   // rhs = -R_T
+    if (p.shard && c->lin_kind == FSE_LIN_DENSE)
+        return set_err(c, FSE_EINVAL, "a trajectory shard has no dense Jacobian: use GMRES");
+    const bool dense = !p.shard && (c->lin_kind == FSE_LIN_DENSE || (c->lin_kind == FSE_LIN_AUTO && m <= 16384));
+    c->lin_iters = 0;
+    c->lin_relres = 0.0;
+    c->reduce_failed = false;
+    int lin = FSE_OK;
+    if (dense) {
+        if (m > 16384) return set_err(c, FSE_EINVAL, "outer solve: dense LU limited to 16384 unknowns");
+        rc = ensure_dense(c, m);
+        if (rc) return rc;
+        if (!c->ht_pm) {
+            fse::launch_pmat(c, Pm);
+            c->ht_pm = true;
+        }
+        fse::launch_dense_jac_ht(c, Pm, c->Jd);
+        rc = fse::dense_lu_solve(c, c->Jd, b, (int)m);
+        if (rc) return set_err(c, rc, "singular hyper-time Jacobian");
+        fse::vec_axpby(c, m, 1.0, b, 1.0, z0);
+    } else {
+        int its = 0;
+        double rel = 0.0;
+        lin = gmres_dev(
+            c, m, [c](const double* v, double* o) { jac_apply_ht_dev(c, v, o); }, b, a, c->lin_rtol,
+            c->lin_restart, c->lin_maxit, &its, &rel);
+        c->lin_iters = its;
+        c->lin_relres = rel;
+        if (c->reduce_failed) return set_err(c, FSE_ECUDA, "shard reduction failed");
+        if (lin != FSE_OK && lin != FSE_ENOCONV) return lin;
+        fse::vec_axpby(c, m, 1.0, a, 1.0, z0);
+        if (lin == FSE_ENOCONV) c->err = "GMRES stopped above its tolerance";
+    }
+    cudaMemcpyAsync(zbar0, z0, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step_hypertime");
+    if (rc) return rc;
+    return st != FSE_OK ? st : lin;
+}
+
+// ----------------------------------------------------------------------------
+// a priori unknown base frequencies (Sec. 3.2: Eq. Cont1, 18, 19, 23, 24)
+// ----------------------------------------------------------------------------
+
+extern "C" int fse_set_rho(fse_ctx* c, const double* rho) {
+    if (!c || !rho) return FSE_EINVAL;
+    const int dm1 = c->p.d - 1;
+    for (int j = 0; j < dm1; ++j)
+        if (!std::isfinite(rho[j])) return set_err(c, FSE_EINVAL, "rho not finite");
+    bool same = true;
+    for (int j = 0; j < dm1; ++j) same = same && c->rho[j] == rho[j];
+    if (same) return FSE_OK;
+    cudaSetDevice(c->device);
+    for (int j = 0; j < dm1; ++j) c->rho[j] = rho[j];
+    std::vector<double> rcv, rsv;
+    rotation_tables(c, rcv, rsv);
+    cudaMemcpyAsync(c->d.rc, rcv.data(), rcv.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d.rs, rsv.data(), rsv.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    fse::launch_fill_tables(c);
+    c->ht_pm = false;
+    c->have_jac = false;   // the stored Jacobian belongs to the previous rotation
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "set_rho");
+}
+
+extern "C" int fse_newton_step_unknown(fse_ctx* c, double* Z0, double w, double* rho, const int* unknown,
+                                       double* res_norm) {
+    if (!c || !Z0 || !rho || !unknown) return FSE_EINVAL;
+    const Params& p = c->p;
+    const int dm1 = p.d - 1;
+    int idx[FSE_MAX_D - 1], u = 0;
+    for (int j = 0; j < dm1; ++j)
+        if (unknown[j]) {
+            // forcing component j + 1 (0-based) moves its phase with rho_j (Eq. E1): then w_{j+2} is set
+            if (j + 1 < p.e) return set_err(c, FSE_EINVAL, "a forced frequency cannot be an unknown");
+            idx[u++] = j;
+        }
+    int rc = fse_set_rho(c, rho);
+    if (rc) return rc;
+    cudaSetDevice(c->device);
+    const size_t m = (size_t)2 * p.n * p.U, M = m + u;
+    if (!c->unk) {
+        cudaError_t e = cudaMalloc(&c->unk, (2 * (size_t)(FSE_MAX_D - 1) * m + 2 * (m + FSE_MAX_D)) * 8);
+        if (e != cudaSuccess) {
+            c->unk = nullptr;
+            return cuda_check(c, e, "unknown-frequency buffers");
+        }
+    }
+    double* cols = c->unk;
+    double* rows = cols + (size_t)(FSE_MAX_D - 1) * m;
+    double* xs = rows + (size_t)(FSE_MAX_D - 1) * m;   // solution (M)
+    double* bs = xs + m + FSE_MAX_D;                   // right-hand side (M)
+    cudaMemcpyAsync(c->d.Z0, Z0, m * 8, cudaMemcpyHostToDevice, c->stream);
+    const int st = eval_at_iterate(c, w, 1, res_norm, nullptr);
+    if (st < 0 && st != FSE_ENOCONV) return st;
+    for (int a = 0; a < u; ++a)
+        fse::launch_unknown_border(c, idx[a], w, c->d.R, c->d.Z0, cols + (size_t)a * m, rows + (size_t)a * m);
+    // rhs = -[R; 0]
+    fse::vec_axpby(c, m, -1.0, c->d.R, 0.0, bs);
+    if (u) cudaMemsetAsync(bs + m, 0, u * 8, c->stream);
+    if (p.shard && c->lin_kind == FSE_LIN_DENSE)
+        return set_err(c, FSE_EINVAL, "a trajectory shard has no dense Jacobian: use GMRES");
+    const bool dense = !p.shard && (c->lin_kind == FSE_LIN_DENSE || (c->lin_kind == FSE_LIN_AUTO && M <= 16384));
+    c->lin_iters = 0;
+    c->lin_relres = 0.0;
+    c->reduce_failed = false;
+    int lin = FSE_OK;
+    if (dense) {
+        if (M > 16384) return set_err(c, FSE_EINVAL, "outer solve: dense LU limited to 16384 unknowns");
+        rc = ensure_dense(c, M);
+        if (rc) return rc;
+        fse::launch_dense_jac_bordered(c, u, cols, rows, c->Jd);
+        rc = fse::dense_lu_solve(c, c->Jd, bs, (int)M);
+        if (rc) return set_err(c, rc, "singular bordered shooting Jacobian");
+        cudaMemcpyAsync(xs, bs, M * 8, cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+        // [J cols; rows^T 0] x: J x_Z + sum_a cols_a x_a, rows_a . x_Z
+        auto Av = [c, m, u, cols, rows](const double* x, double* y) {
+            jac_apply_dev(c, x, y);
+            if (u) {
+                fse::vec_mupdate(c, m, u, cols, x + m, y);
+                fse::vec_mdot(c, m, u, rows, x, y + m);
+            }
+        };
+        int its = 0;
+        double rel = 0.0;
+        lin = gmres_dev(c, M, Av, bs, xs, c->lin_rtol, c->lin_restart, c->lin_maxit, &its, &rel);
+        c->lin_iters = its;
+        c->lin_relres = rel;
+        if (c->reduce_failed) return set_err(c, FSE_ECUDA, "shard reduction failed");
+        if (lin != FSE_OK && lin != FSE_ENOCONV) return lin;
+        if (lin == FSE_ENOCONV) c->err = "GMRES stopped above its tolerance";
+    }
+    fse::vec_axpby(c, m, 1.0, xs, 1.0, c->d.Z0);   // Z0 += dZ
+    double dw[FSE_MAX_D - 1] = {0.0};
+    if (u) cudaMemcpyAsync(dw, xs + m, u * 8, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(Z0, c->d.Z0, m * 8, cudaMemcpyDeviceToHost, c->stream);
+    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "newton_step_unknown");
+    if (rc) return rc;
+    for (int a = 0; a < u; ++a) rho[idx[a]] += dw[a] / w;   // w_{j+2} = rho_j w_1 with w_1 fixed
+    return st != FSE_OK ? st : lin;
+}
+
 extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, int h, double* sigma) {
+    if (c && c->p.shard) return set_err(c, FSE_EINVAL, "not available on a trajectory shard");
     if (!c || !Z0 || !sigma) return FSE_EINVAL;
     if (N_Ly < 1 || h < 1 || h > 64 || h > 2 * c->p.n) return set_err(c, FSE_EINVAL, "need N_Ly >= 1, 1 <= h <= min(64, 2n)");
     cudaSetDevice(c->device);
@@ -1062,6 +1397,7 @@ extern "C" int fse_lyapunov(fse_ctx* c, const double* Z0, double w, int N_Ly, in
 }
 
 extern "C" int fse_lyapunov_noalloc(fse_ctx* c, const double* Z0, double w, int N_Ly, int h, double* sigma) {
+    if (c && c->p.shard) return set_err(c, FSE_EINVAL, "not available on a trajectory shard");
     if (!c || !Z0 || !sigma) return FSE_EINVAL;
     if (N_Ly < 1 || h < 1 || h > 64 || h > 2 * c->p.n)
         return set_err(c, FSE_EINVAL, "need N_Ly >= 1, 1 <= h <= min(64, 2n)");
@@ -1251,6 +1587,7 @@ extern "C" int fse_batch_residual_jacobian(fse_batch* b, const double* const* Z0
 
 extern "C" int fse_continue_arclength(fse_ctx* c, const fse_arc_opts* o, const double* Z_start, double* Z_out,
                                       double* omega_out, fse_cont_point* info, int* n_done) {
+    if (c && c->p.shard) return set_err(c, FSE_EINVAL, "not available on a trajectory shard");
     if (!c || !o || !Z_start || o->n_points < 1) return FSE_EINVAL;
     if (n_done) *n_done = 0;
     if (!(o->rel_tol > 0.0) || o->max_newton < 1 || !(o->ds > 0.0) || !(o->omega_start > 0.0))
@@ -1437,6 +1774,24 @@ extern "C" int fse_continue_arclength(fse_ctx* c, const fse_arc_opts* o, const d
 extern "C" int fse_set_steps(fse_ctx* c, int n_steps) {
     if (!c || n_steps < 0) return FSE_EINVAL;
     c->n_steps = n_steps;
+    return FSE_OK;
+}
+
+extern "C" int fse_set_reduce(fse_ctx* c, fse_reduce_fn fn, void* user) {
+    if (!c) return FSE_EINVAL;
+    if (!c->p.shard) return set_err(c, FSE_EINVAL, "not a trajectory shard");
+    c->reduce = fn;
+    c->reduce_user = user;
+    return FSE_OK;
+}
+
+extern "C" int fse_set_tangent_solve(fse_ctx* c, int kind) {
+    if (!c) return FSE_EINVAL;
+    if (kind != FSE_SOLVE_AUTO && kind != FSE_SOLVE_SIMT && kind != FSE_SOLVE_TC)
+        return set_err(c, FSE_EINVAL, "unknown tangent-solve kind");
+    if (kind == FSE_SOLVE_TC && !c->p.tc_ok)
+        return set_err(c, FSE_EINVAL, "tensor-core solves need FP32 tangents and half-bandwidth <= 96");
+    c->solve_kind = kind;
     return FSE_OK;
 }
 

@@ -24,18 +24,27 @@ __device__ __forceinline__ void vk_slope(double xi, double L, double Nd[4]) {
 }
 
 __device__ __forceinline__ int elem_ndof(int type) {
-    return type == FSE_NL_CUBIC_GROUND ? 1 : (type == FSE_NL_CUBIC_DIFF ? 2 : 6);
+    return (type == FSE_NL_CUBIC_GROUND || type == FSE_NL_VDP) ? 1 : (type == FSE_NL_CUBIC_DIFF ? 2 : 6);
 }
 
-// Element force fe[6] (local dof order) and, if ke != nullptr, its tangent ke[36]
-// of the nonlinear elements of Eq. (1): cubic springs and the von Karman beam
-// (gradient of EA/2 int (u' w'^2 + w'^4/4) dx, 5-point Gauss-Legendre).
-__device__ inline void elem_eval(int type, const int* dof, const double* p, const double* q,
-                                 double fe[6], double* ke) {
+// Element force fe[6] (local dof order) and, if ke != nullptr, its tangent ke[36] = d fe / d q
+// and, if ce != nullptr, its velocity tangent ce[36] = d fe / d qdot of the nonlinear elements of
+// Eq. (1): cubic springs, the von Karman beam (gradient of EA/2 int (u' w'^2 + w'^4/4) dx,
+// 5-point Gauss-Legendre) and the self-excited damper f = p0 (q^2 - 1) qdot.  qd holds the
+// physical velocities qdot = w_1 u of the dofs (nullptr: zero).
+__device__ inline void elem_eval(int type, const int* dof, const double* p, const double* q, const double* qd,
+                                 double fe[6], double* ke, double* ce = nullptr) {
     for (int a = 0; a < 6; ++a) fe[a] = 0.0;
     if (ke)
         for (int a = 0; a < 36; ++a) ke[a] = 0.0;
-    if (type == FSE_NL_CUBIC_GROUND) {
+    if (ce)
+        for (int a = 0; a < 36; ++a) ce[a] = 0.0;
+    if (type == FSE_NL_VDP) {
+        const double x = qval(q, dof[0]), v = qd ? qval(qd, dof[0]) : 0.0;
+        fe[0] = p[0] * (x * x - 1.0) * v;
+        if (ke) ke[0] = 2.0 * p[0] * x * v;
+        if (ce) ce[0] = p[0] * (x * x - 1.0);
+    } else if (type == FSE_NL_CUBIC_GROUND) {
         const double x = qval(q, dof[0]);
         fe[0] = p[0] * x * x * x;
         if (ke) ke[0] = 3.0 * p[0] * x * x;
@@ -138,6 +147,58 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"((int)sizeof(T)));
 }
+
+// ---- mbarrier / bulk-copy helpers (every wait is bounded: after about 2 s of SM clock the
+// waiting thread raises the error flag and gives up)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned tx) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
+                 "r"(tx)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
+    const unsigned a = smem_addr(bar);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1ll << 32)) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 3-D tiled TMA load (box of the tensor map at {x, y, z}) completing on bar; the shared
+// destination is 128-byte aligned and x * element size a multiple of 16 bytes
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
 
 // grid of a grid-stride loop: enough blocks for `total` items, at most per_sm blocks per SM
 static inline int nblocks(size_t total, int bs, int per_sm = 16) {

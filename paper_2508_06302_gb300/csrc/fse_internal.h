@@ -69,6 +69,10 @@ struct Dev {
     int* kt_src = nullptr;   // element * 36 + a * 6 + b
     double* ke = nullptr;    // N x n_el x 36 element tangents (scratch of k_state)
     void* kt_val = nullptr;  // FSE_NBUF_KT x N x kt_ld
+    // velocity tangents C_t = d f_nl / d qdot of the velocity-dependent elements (only when the
+    // model has some): element scratch N x n_el x 36 and the values on the K_t pattern, same ring
+    double* ce = nullptr;
+    void* ct_val = nullptr;  // FSE_NBUF_KT x N x kt_ld
     void* romega = nullptr;  // 2 x N x n   right-hand side of the w_1 column
     // AFT tables
     double* phis = nullptr;  // N x (d-1)
@@ -97,6 +101,11 @@ struct Dev {
     // Rb = [L(i0 + 32 + c, i0 + r) at c * 32 + r | Dinv]; entries outside the band stay zero
     void* Rf = nullptr;
     void* Rb = nullptr;
+    // factor records of the tensor-core solves (FP32 tangents, b <= 96), per direction
+    // N x (nblk + 1) x 8192 floats: record sigma + 1 holds the four B operands (hi | lo, K-major)
+    // of the MMAs issued after block sigma (fse_tc.cu)
+    void* Tf = nullptr;
+    void* Tb = nullptr;
     // tangents (sensitivity precision)
     void* X = nullptr;       // N x n x ld (columns P..ld-1 are zero padding)
     void* V = nullptr;
@@ -116,6 +125,10 @@ struct Dev {
 
 struct Params {
     int n = 0, b = 0, d = 0, e = 0, N = 0, U = 0, L = 0, S1 = 0, P = 0;
+    // trajectory shard: this context integrates samples s0 .. s0 + N - 1 of an N_glob-sample grid;
+    // its DFT sums are then partial and complete only after the reduction across shards
+    int N_glob = 0, s0 = 0;
+    bool shard = false;
     int maxit = 0, prec = 0, ncolors = 0, n_el = 0, nnz = 0, nnz_kt = 0, nblk = 0;
     int ld = 0;              // row stride of the tangent arrays: P rounded up to a multiple of 4
     int RW = 0;              // ring rows of the right-hand-side kernel (two passes + 2b)
@@ -125,6 +138,9 @@ struct Params {
     int MK = 0;              // K_t entries of a pass's slice (max, a multiple of 4)
     int RWT = 0;             // ring rows of the blocked solves (power of two >= b + 32)
     int RECE = 0;            // elements of one block record of Rf / Rb: bpad * 32 + 32 * 32
+    int ND = 0;              // 32-row blocks coupled to a block through the band: ceil(b / 32)
+    bool tc_ok = false;      // the tensor-core solves apply (FP32 tangents, b <= 96)
+    bool has_vel = false;    // some element depends on qdot (C_t != 0)
     double tol = 0;
     size_t smem_state = 0, smem_rhs = 0, smem_trsm = 0;
 };
@@ -169,6 +185,18 @@ struct fse_ctx {
     size_t kry_cap = 0;
     int lin_iters = 0;
     double lin_relres = 0.0;
+    int solve_kind = FSE_SOLVE_AUTO;   // banded tangent solves: FSE_SOLVE_AUTO / _SIMT / _TC
+    // hyper-time form (Sec. 3.4), allocated on first use: start points, residual and two scratch
+    // vectors (N x 2n each), a coefficient vector (2n U~) and Gamma R Gamma^-1 (N x N)
+    double* ht = nullptr;
+    bool ht_pm = false;                // Gamma R Gamma^-1 formed
+    // unknown base frequencies (Sec. 3.2), allocated on first use: u border columns, u rows and
+    // a GMRES-size solution / right-hand side ((2n U~ + 3) each, u <= 3)
+    double* unk = nullptr;
+    // reduction of partial DFT sums across trajectory shards (fse_set_reduce), nullable
+    fse_reduce_fn reduce = nullptr;
+    void* reduce_user = nullptr;
+    bool reduce_failed = false;
 };
 
 namespace fse {
@@ -230,9 +258,23 @@ void launch_domega(fse_ctx* c, double* zout);
 void launch_phi_copy(fse_ctx* c, double* Phi_dev, double* dzdw_dev);
 void launch_phi_copy_one(fse_ctx* c, int s, double* Phi_dev, double* dzdw_dev);
 void launch_dense_jac(fse_ctx* c, double* J);
+// unknown base frequency w_{j+2} (Sec. 3.2): its column dR/dw (Eq. 23, 24) and phase-condition row
+// (Eq. 18, 19) from R and Z0 (2n U~ each); the dense J bordered by u such columns and rows
+void launch_unknown_border(fse_ctx* c, int j, double w, const double* R, const double* Z0, double* col,
+                           double* row);
+void launch_dense_jac_bordered(fse_ctx* c, int u, const double* cols, const double* rows, double* B);
+// hyper-time form (Sec. 3.4): Pm = Gamma R Gamma^-1 (N x N) and the dense Jacobian of Eq. FSES_T
+void launch_pmat(fse_ctx* c, double* Pm);
+void launch_dense_jac_ht(fse_ctx* c, const double* Pm, double* J);
 // (m + 1) x (m + 1) pseudo-arclength matrix [J dR/dw_1; t_Z^T tail] (row-major)
 void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double tail, double* B);
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
+// tensor-core tangent solves (fse_tc.cu): dynamic shared memory, per-step factor records (both
+// directions, from the factor of step k) and the forward (phase 1) / backward (phase 2) solve
+size_t tc_smem();
+void launch_tc_records(fse_ctx* c, int k, cudaStream_t st);
+void launch_tc_solve(fse_ctx* c, int phase, cudaStream_t st);
+inline bool use_tc(const fse_ctx* c) { return c->p.tc_ok && c->solve_kind != FSE_SOLVE_SIMT; }
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
 // same propagation with the static device scratch of fse_aft.cu (no allocation)
 int lyapunov_run_noalloc(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);

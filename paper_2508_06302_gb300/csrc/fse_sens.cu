@@ -71,57 +71,6 @@ __device__ __forceinline__ void st4(T* p, const T v[4]) {
 }
 
 
-// ---- mbarrier / bulk-copy helpers (every wait is bounded: after about 2 s of SM clock the
-// waiting thread raises the error flag and gives up)
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned tx) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
-                 "r"(tx)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
-    const unsigned a = smem_addr(bar);
-    const long long t0 = clock64();
-    while (true) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > (1ll << 32)) {
-            atomicExch(err, 1);
-            return false;
-        }
-    }
-}
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) completing on bar
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// 3-D tiled TMA load (box of the tensor map at {x, y, z}) completing on bar; the shared
-// destination is 128-byte aligned and x * element size a multiple of 16 bytes
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                          unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-        : "memory");
-}
-
 // explicit shared-memory loads on 32-bit shared addresses
 __device__ __forceinline__ uint4 lds_u4(unsigned a) {
     uint4 v;
@@ -851,6 +800,33 @@ __global__ void __launch_bounds__(256, 1) k_trsm8(SensArgs A) {
     }
 }
 
+// Velocity-dependent elements (C_t = d f_nl / d qdot != 0): the right-hand side of the tangent
+// step gains (w 2/D C_t(k+1)) X_k + w (C_t(k+1) - C_t(k)) V_k (the linearised equation of motion of
+// step k eliminates the acceleration tangent as in the C_t = 0 case, and the velocity tangent of
+// the new step enters through u' = 2/D (q' - q_k') - u_k').  C_t lives on the K_t pattern; one
+// thread per tangent column, rows without velocity-tangent entries are skipped.
+template <typename T>
+__global__ void k_ct_rhs(int n, int ld, int kt_ld, double wa2, double w, const int* __restrict__ kt_ptr,
+                         const int* __restrict__ kt_col, const T* __restrict__ c1, const T* __restrict__ c0,
+                         const T* __restrict__ X, const T* __restrict__ V, T* Y) {
+    const int s = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ld) return;
+    const size_t base = (size_t)s * n * ld;
+    const T* C1 = c1 + (size_t)s * kt_ld;
+    const T* C0 = c0 + (size_t)s * kt_ld;
+    for (int i = 0; i < n; ++i) {
+        const int e0 = kt_ptr[i], e1 = kt_ptr[i + 1];
+        if (e0 == e1) continue;
+        double acc = 0.0;
+        for (int e = e0; e < e1; ++e) {
+            const size_t o = base + (size_t)kt_col[e] * ld + t;
+            acc += wa2 * (double)C1[e] * (double)X[o] + w * ((double)C1[e] - (double)C0[e]) * (double)V[o];
+        }
+        Y[base + (size_t)i * ld + t] = T((double)Y[base + (size_t)i * ld + t] + acc);
+    }
+}
+
 // X_0 = [I 0 0], V_0 = [0 I 0], zero padding columns
 template <typename T>
 __global__ void k_sens_init(int N, int n, int ld, T* X, T* V) {
@@ -1039,7 +1015,32 @@ void launch_sens_phase(fse_ctx* c, int k, double w, int phase, cudaStream_t st) 
     A.X = c->d.X;
     A.V = c->d.V;
     A.Y = c->d.Y;
-    (void)w;
+    if (phase == 0 && p.has_vel) {
+        // the plain right-hand side first, then the velocity-tangent terms on top of it
+        if (p.prec == FSE_MIXED_FP32)
+            sens_launch<float>(c, A, 0, st);
+        else
+            sens_launch<double>(c, A, 0, st);
+        const size_t csz = (size_t)p.N * p.kt_ld * tsz;
+        const void* c1 = (const char*)c->d.ct_val + ((k + 1) % FSE_NBUF_KT) * csz;
+        const void* c0 = (const char*)c->d.ct_val + (k % FSE_NBUF_KT) * csz;
+        const dim3 g((p.ld + 127) / 128, p.N);
+        const double wa2 = w * 2.0 / Dl;
+        if (p.prec == FSE_MIXED_FP32)
+            k_ct_rhs<float><<<g, 128, 0, st>>>(p.n, p.ld, p.kt_ld, wa2, w, c->d.kt_ptr, c->d.kt_col,
+                                               (const float*)c1, (const float*)c0, (const float*)c->d.X,
+                                               (const float*)c->d.V, (float*)c->d.Y);
+        else
+            k_ct_rhs<double><<<g, 128, 0, st>>>(p.n, p.ld, p.kt_ld, wa2, w, c->d.kt_ptr, c->d.kt_col,
+                                                (const double*)c1, (const double*)c0, (const double*)c->d.X,
+                                                (const double*)c->d.V, (double*)c->d.Y);
+        return;
+    }
+    if (phase > 0 && use_tc(c)) {
+        if (phase == 1) launch_tc_records(c, k, st);
+        launch_tc_solve(c, phase, st);
+        return;
+    }
     if (p.prec == FSE_MIXED_FP32)
         sens_launch<float>(c, A, phase, st);
     else

@@ -31,7 +31,9 @@ void ensure_constants() {
 // AFT tables (App. D, Eq. 14) and per-w_1 operators
 // ----------------------------------------------------------------------------
 
-__global__ void k_tables(int N, int U, int dm1, const int* __restrict__ ktab,
+// (the sums over samples of Eq. D3 are normalised by the whole grid's Nglob; a trajectory shard
+// holds its own N columns of Gamma^-1)
+__global__ void k_tables(int N, int Nglob, int U, int dm1, const int* __restrict__ ktab,
                          const double* __restrict__ phis, const double* __restrict__ rc,
                          const double* __restrict__ rs, double* G, double* Gi, double* RG) {
     const int s = blockIdx.x;
@@ -46,7 +48,7 @@ __global__ void k_tables(int N, int U, int dm1, const int* __restrict__ ktab,
             g = ((c - 1) & 1) ? sin(arg) : cos(arg);
         }
         G[(size_t)s * U + c] = g;
-        Gi[(size_t)c * N + s] = (c == 0 ? 1.0 : 2.0) * g / (double)N;
+        Gi[(size_t)c * N + s] = (c == 0 ? 1.0 : 2.0) * g / (double)Nglob;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < U; c += blockDim.x) {
@@ -357,6 +359,10 @@ struct StateArgs {
     const int *kt_ptr, *kt_col, *kt_soff, *kt_src;
     double* ke;
     void* kt_out;       // N x kt_ld, K_t at the new state
+    int has_vel;        // velocity-dependent elements present: C_t values and the velocity vector
+    double* ce;         // N x n_el x 36 element velocity tangents (scratch), when has_vel
+    void* ct_out;       // N x kt_ld, C_t at the new state (same pattern and ring as K_t)
+    const void* ct_prev;   // N x kt_ld, C_t at the previous state
     void* romega;       // N x n, w_1-column term of this step (regular steps)
     const double *LMc, *LMr, *LMinv;
     double *q, *u, *a;
@@ -374,15 +380,16 @@ __device__ __forceinline__ double forcing_i(const StateArgs& A, int s, int i, do
     return e;
 }
 
-// r += f_nl(q), elements processed colour by colour (no two elements of a colour share a dof)
-__device__ void add_fnl(const StateArgs& A, const double* q, double* r) {
+// r += f_nl(q, qdot), elements processed colour by colour (no two elements of a colour share a
+// dof); qd: physical velocities (nullptr when no element depends on them)
+__device__ void add_fnl(const StateArgs& A, const double* q, const double* qd, double* r) {
     for (int c = 0; c < A.ncolors; ++c) {
         const int e0 = A.col_off[c], e1 = A.col_off[c + 1];
         for (int el = e0 + threadIdx.x; el < e1; el += blockDim.x) {
             const int type = A.el_type[el];
             const int* dof = A.el_dof + 6 * el;
             double fe[6];
-            elem_eval(type, dof, A.el_p + 6 * el, q, fe, nullptr);
+            elem_eval(type, dof, A.el_p + 6 * el, q, qd, fe, nullptr);
             const int nd = elem_ndof(type);
             for (int a = 0; a < nd; ++a)
                 if (dof[a] >= 0) r[dof[a]] += fe[a];
@@ -391,14 +398,18 @@ __device__ void add_fnl(const StateArgs& A, const double* q, double* r) {
     }
 }
 
-// Ac = lower column band of S + K_t(q) (type T), kt_out = K_t(q) values on its CSR pattern.
+// Ac = lower column band of K_eff = S + K_t(q, qdot) + w (2/Delta) C_t(q, qdot) (type T), kt_out =
+// K_t values on its CSR pattern and, with velocity-dependent elements, ct_out = C_t values on it.
 template <typename T>
-__device__ void assemble_keff(const StateArgs& A, int s, const double* q, T* Ac, T* kt_out) {
+__device__ void assemble_keff(const StateArgs& A, int s, const double* q, const double* qd, T* Ac, T* kt_out,
+                              T* ct_out) {
     const int n = A.n, b = A.b, nb = b + 1;
     double* ke = A.ke + (size_t)s * A.n_el * 36;
+    double* ce = A.has_vel ? A.ce + (size_t)s * A.n_el * 36 : nullptr;
     for (int el = threadIdx.x; el < A.n_el; el += blockDim.x) {
         double fe[6];
-        elem_eval(A.el_type[el], A.el_dof + 6 * el, A.el_p + 6 * el, q, fe, ke + (size_t)el * 36);
+        elem_eval(A.el_type[el], A.el_dof + 6 * el, A.el_p + 6 * el, q, qd, fe, ke + (size_t)el * 36,
+                  ce ? ce + (size_t)el * 36 : nullptr);
     }
     for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) Ac[idx] = T(0);
     __syncthreads();
@@ -413,10 +424,15 @@ __device__ void assemble_keff(const StateArgs& A, int s, const double* q, T* Ac,
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int e1 = A.kt_ptr[i + 1];
         for (int e = A.kt_ptr[i]; e < e1; ++e) {
-            double v = 0.0;
+            double v = 0.0, vc = 0.0;
             const int s1 = A.kt_soff[e + 1];
             for (int k = A.kt_soff[e]; k < s1; ++k) v += ke[A.kt_src[k]];
             kt_out[e] = T(v);
+            if (ce) {
+                for (int k = A.kt_soff[e]; k < s1; ++k) vc += ce[A.kt_src[k]];
+                ct_out[e] = T(vc);
+                v += A.w * A.a2c * vc;   // d u / d q = 2 / Delta, d qdot / d u = w
+            }
             const int j = A.kt_col[e];
             if (j <= i) {
                 const size_t o = (size_t)j * nb + (i - j);
@@ -601,6 +617,10 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     T* stg = wnd + (size_t)(nb + 1) * nb;
     const size_t wspan = max((size_t)(nb + 1 + FSE_CHOL_PF) * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
     T* ysol = wnd + wspan;                                // n: solve vector in the factor precision
+    // physical velocities qdot = w u of the current iterate (velocity-dependent elements only)
+    double* sv = A.has_vel
+                     ? reinterpret_cast<double*>((reinterpret_cast<size_t>(ysol + n) + 7) & ~static_cast<size_t>(7))
+                     : nullptr;
     __shared__ int s_conv, s_stat;
     const size_t off = (size_t)s * n;
     const size_t foff = (size_t)s * n * nb;
@@ -612,6 +632,13 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     T* oRf = reinterpret_cast<T*>(A.oRf) + (size_t)s * A.nblk * A.RECE;
     T* oRb = reinterpret_cast<T*>(A.oRb) + (size_t)s * A.nblk * A.RECE;
     T* kt_out = reinterpret_cast<T*>(A.kt_out) + (size_t)s * A.kt_ld;
+    T* ct_out = A.has_vel ? reinterpret_cast<T*>(A.ct_out) + (size_t)s * A.kt_ld : nullptr;
+    // sv = w u at the state (sq, su), or, in the step, at u(q) = 2/Delta (q - q_k) - u_k
+    auto vel_state = [&]() {
+        if (!sv) return;
+        for (int i = tid; i < n; i += nt) sv[i] = A.w * su[i];
+        __syncthreads();
+    };
     if (tid == 0) {
         s_stat = A.init ? 0 : A.status[s];
         s_conv = 0;
@@ -627,7 +654,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         // consistent start: w^2 M a0 = e(0) - w D u0 - K q0 - f_nl(q0)  (Eq. E2 at phi_1 = 0)
         for (int i = tid; i < n; i += nt) sr[i] = 0.0;
         __syncthreads();
-        add_fnl(A, sq, sr);
+        vel_state();
+        add_fnl(A, sq, sv, sr);
         for (int i = tid; i < n; i += nt)
             sb[i] = forcing_i(A, s, i, 0.0) - A.w * csr_row(A.cs_ptr, A.cs_col, A.cs_d, i, su) -
                     csr_row(A.cs_ptr, A.cs_col, A.cs_k, i, sq) - sr[i];
@@ -666,10 +694,16 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         // Newton on Eq. (E6): starts as a chord iteration with the factor of K_eff(q_k) and
         // refactors at the current iterate whenever the contraction ratio exceeds 0.1
         double prev = -1.0;
+        auto vel_iterate = [&]() {
+            if (!sv) return;
+            for (int i = tid; i < n; i += nt) sv[i] = A.w * (A.a2c * (sqn[i] - sq[i]) - su[i]);
+            __syncthreads();
+        };
         for (it = 0; it < A.maxit; ++it) {
             for (int i = tid; i < n; i += nt) sr[i] = csr_row(A.cs_ptr, A.cs_col, A.cs_s, i, sqn) - sb[i];
             __syncthreads();
-            add_fnl(A, sqn, sr);
+            vel_iterate();
+            add_fnl(A, sqn, sv, sr);
             cta_blocked_solve<T>(cLc, cLr, cDi, n, b, A.nblk, sr, ysol, tmp);
             double dmax = 0.0, qmax = 0.0;
             for (int i = tid; i < n; i += nt) {
@@ -693,7 +727,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             const bool allow = sizeof(T) == 8 || nref == 0;
             if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
                 ++nref;
-                assemble_keff<T>(A, s, sqn, oLc, kt_out);
+                vel_iterate();
+                assemble_keff<T>(A, s, sqn, sv, oLc, kt_out, ct_out);
                 if (band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
@@ -734,7 +769,24 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     // effective stiffness at the new state, its banded Cholesky factor and block inverses
     int bad = 0;
     if (A.refactor) {
-        assemble_keff<T>(A, s, sq, oLc, kt_out);
+        vel_state();
+        assemble_keff<T>(A, s, sq, sv, oLc, kt_out, ct_out);
+        if (A.has_vel && !A.init) {
+            // velocity-dependent elements add - C_t(k+1) u_{k+1} - C_t(k) u_k to the w_1 column
+            // (d f / d w_1 = C_t u at both ends of the step); sb holds u_k + u_{k+1}, su u_{k+1}
+            __syncthreads();
+            T* rom = reinterpret_cast<T*>(A.romega) + off;
+            const T* cp = reinterpret_cast<const T*>(A.ct_prev) + (size_t)s * A.kt_ld;
+            for (int i = tid; i < n; i += nt) {
+                double acc = 0.0;
+                const int e1 = A.kt_ptr[i + 1];
+                for (int e = A.kt_ptr[i]; e < e1; ++e) {
+                    const int j = A.kt_col[e];
+                    acc += (double)ct_out[e] * su[j] + (double)cp[e] * (sb[j] - su[j]);
+                }
+                rom[i] = T((double)rom[i] - acc);
+            }
+        }
         bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE);
         if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
     }
@@ -771,7 +823,7 @@ __global__ void k_factor_M(int n, int b, const double* Mb, double* LMc, double* 
 void launch_fill_tables(fse_ctx* c) {
     ensure_constants();
     const Params& p = c->p;
-    k_tables<<<p.N, 128, 0, c->stream>>>(p.N, p.U, p.d - 1, c->d.ktab, c->d.phis, c->d.rc, c->d.rs,
+    k_tables<<<p.N, 128, 0, c->stream>>>(p.N, p.N_glob, p.U, p.d - 1, c->d.ktab, c->d.phis, c->d.rc, c->d.rs,
                                          c->d.G, c->d.Gi, c->d.RG);
 }
 
@@ -807,7 +859,7 @@ size_t state_smem(const Params& p) {
     const int nb = p.b + 1;
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
     const size_t wspan = std::max((size_t)(nb + 1 + FSE_CHOL_PF) * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
-    return (size_t)(6 * p.n + FSE_BLK) * 8 + (wspan + (size_t)p.n) * tsz;
+    return (size_t)(6 * p.n + FSE_BLK) * 8 + (wspan + (size_t)p.n) * tsz + (p.has_vel ? (size_t)p.n * 8 + 8 : 0);
 }
 
 static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
@@ -850,6 +902,8 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.kt_soff = c->d.kt_soff;
     A.kt_src = c->d.kt_src;
     A.ke = c->d.ke;
+    A.has_vel = p.has_vel ? 1 : 0;
+    A.ce = c->d.ce;
     const size_t ktsz = (size_t)p.N * p.kt_ld * tsz;
     const size_t fsz = (size_t)p.N * p.n * (p.b + 1) * tsz;
     const size_t vsz = (size_t)p.N * p.n * tsz;
@@ -859,6 +913,9 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     const int kt_idx = (k + 1) % FSE_NBUF_KT;
     const int fo = ((k % 2) + 2) % 2, fi = 1 - fo;
     A.kt_out = (char*)c->d.kt_val + kt_idx * ktsz;
+    A.ct_out = p.has_vel ? (char*)c->d.ct_val + kt_idx * ktsz : nullptr;
+    A.ct_prev = p.has_vel ? (const char*)c->d.ct_val + (size_t)(((k % FSE_NBUF_KT) + FSE_NBUF_KT) % FSE_NBUF_KT) * ktsz
+                          : nullptr;
     A.romega = (char*)c->d.romega + (size_t)fo * vsz;
     A.LMc = c->d.LMc;
     A.LMr = c->d.LMr;

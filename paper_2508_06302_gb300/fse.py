@@ -29,6 +29,10 @@ FSE_MIXED_FP32 = 1
 FSE_LIN_AUTO = 0
 FSE_LIN_DENSE = 1
 FSE_LIN_GMRES = 2
+FSE_NL_VDP = 4
+FSE_SOLVE_AUTO = 0
+FSE_SOLVE_SIMT = 1
+FSE_SOLVE_TC = 2
 
 _PREC = {"fp64": FSE_FP64, "mixed_fp32": FSE_MIXED_FP32, "fp32": FSE_MIXED_FP32}
 
@@ -95,6 +99,16 @@ def load(path: Optional[str] = None):
         "fse_lyapunov_noalloc": (ctypes.c_int, [_VP, _DP, ctypes.c_double, ctypes.c_int, ctypes.c_int, _DP]),
         "fse_set_linear_solver": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
         "fse_linear_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+        "fse_set_tangent_solve": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fse_residual_jacobian_hypertime": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP, ctypes.c_int, _IP,
+                                                           _IP]),
+        "fse_jacobian_apply_hypertime": (ctypes.c_int, [_VP, _DP, _DP, ctypes.c_int]),
+        "fse_newton_step_hypertime": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP]),
+        "fse_set_rho": (ctypes.c_int, [_VP, _DP]),
+        "fse_setup_shard": (ctypes.c_int, [ctypes.POINTER(fse_model), ctypes.POINTER(fse_opts), ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "fse_set_reduce": (ctypes.c_int, [_VP, REDUCE_FN, _VP]),
+        "fse_newton_step_unknown": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP, _IP, _DP]),
         "fse_timings": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
         "fse_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
         "fse_set_steps": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -140,6 +154,10 @@ def _f64_vector(a, size, what):
     return v
 
 
+# int (*fse_reduce_fn)(void* user, double* buf_dev, size_t count, void* stream)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
 class FSEError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("FSE error %d: %s" % (code, msg))
@@ -151,8 +169,9 @@ class FSEError(RuntimeError):
 # ----------------------------------------------------------------------------
 
 def fse_setup(model, d, S, H, rho, S1, newton_tol=1e-10, newton_maxit=20, precision="fp64",
-              device=-1):
-    """fse_setup(): returns an opaque context handle (int)."""
+              device=-1, shard=None):
+    """fse_setup() (fse_setup_shard() for shard = (s_begin, s_end)): returns an opaque context
+    handle (int)."""
     lib = load()
     M = np.ascontiguousarray(model.M, dtype=np.float64)
     D = np.ascontiguousarray(model.D, dtype=np.float64)
@@ -172,7 +191,11 @@ def fse_setup(model, d, S, H, rho, S1, newton_tol=1e-10, newton_maxit=20, precis
     prec = _PREC[precision] if isinstance(precision, str) else int(precision)
     fo = fse_opts(int(d), _ip(Sa), _ip(Ha), _dp(ra), int(S1), float(newton_tol), int(newton_maxit), prec)
     h = _VP()
-    rc = lib.fse_setup(ctypes.byref(fm), ctypes.byref(fo), int(device), ctypes.byref(h))
+    if shard is None:
+        rc = lib.fse_setup(ctypes.byref(fm), ctypes.byref(fo), int(device), ctypes.byref(h))
+    else:
+        rc = lib.fse_setup_shard(ctypes.byref(fm), ctypes.byref(fo), int(shard[0]), int(shard[1]), int(device),
+                                 ctypes.byref(h))
     if rc != FSE_OK:
         raise FSEError(rc, lib.fse_last_error(None).decode())
     return h.value
@@ -198,11 +221,30 @@ class Context:
     """One FSE-Shooting problem on one GPU (owns an ``fse_ctx``)."""
 
     def __init__(self, model, d, S, H, rho, S1, newton_tol=1e-10, newton_maxit=20,
-                 precision="fp64", device=-1):
-        self.h = fse_setup(model, d, S, H, rho, S1, newton_tol, newton_maxit, precision, device)
+                 precision="fp64", device=-1, shard=None):
+        self.h = fse_setup(model, d, S, H, rho, S1, newton_tol, newton_maxit, precision, device, shard)
         self.n_unknowns, self.U, self.N, self.n, self.band = fse_sizes(self.h)
         self.d = d
         self.precision = precision
+        self.shard = shard
+        self._reduce_cb = None     # keeps the ctypes callback alive while the library holds it
+
+    def set_reduce(self, fn):
+        """fse_set_reduce with a Python callable fn(ptr, count, stream) -> None that leaves the sum
+        over all shards of the `count` doubles at device address ptr in place (None clears it)."""
+        if fn is None:
+            self._check(load().fse_set_reduce(self.h, None, None))
+            self._reduce_cb = None
+            return
+
+        def _cb(user, ptr, count, stream):
+            try:
+                fn(int(ptr), int(count), int(stream or 0))
+                return 0
+            except Exception:
+                return 1
+        self._reduce_cb = REDUCE_FN(_cb)
+        self._check(load().fse_set_reduce(self.h, self._reduce_cb, None))
 
     @classmethod
     def from_workload(cls, wl, precision="fp64", newton_tol=None, newton_maxit=None, device=-1):
@@ -304,6 +346,67 @@ class Context:
         """fse_set_linear_solver: kind in {"auto", "dense", "gmres"}."""
         k = {"auto": FSE_LIN_AUTO, "dense": FSE_LIN_DENSE, "gmres": FSE_LIN_GMRES}[kind]
         self._check(load().fse_set_linear_solver(self.h, k, float(rel_tol), int(restart), int(max_iters)))
+
+    def _samples(self, zb, what):
+        """A sample-major (N, 2n) array of the hyper-time form, as a contiguous float64 copy."""
+        a = np.ascontiguousarray(zb, dtype=np.float64)
+        if a.size != self.N * 2 * self.n:
+            raise ValueError("%s: expected %d x %d values, got %d" % (what, self.N, 2 * self.n, a.size))
+        return a.reshape(self.N, 2 * self.n).copy()
+
+    def residual_jacobian_hypertime(self, zbar0, omega1, want_jacobian=True, allow_status=(FSE_ENOCONV,)):
+        """fse_residual_jacobian_hypertime(): returns (R_T (N x 2n), traj_status, newton_iters, rc)."""
+        zb = self._samples(zbar0, "zbar0")
+        RT = np.zeros_like(zb)
+        st = np.zeros(self.N, np.int32)
+        it = np.zeros(self.N, np.int32)
+        rc = load().fse_residual_jacobian_hypertime(self.h, _dp(zb), float(omega1), _dp(RT), int(want_jacobian),
+                                                    _ip(st), _ip(it))
+        self._check(rc, allow_status)
+        return RT, st, it, rc
+
+    def jacobian_apply_hypertime(self, V):
+        """fse_jacobian_apply_hypertime() for a stack of vectors (k, N, 2n) or one (N, 2n)."""
+        a = np.ascontiguousarray(V, dtype=np.float64)
+        m = self.N * 2 * self.n
+        if a.size % m or a.size == 0:
+            raise ValueError("V: size must be a positive multiple of N * 2n = %d" % m)
+        k = a.size // m
+        a = a.reshape(k, m)
+        out = np.zeros_like(a)
+        self._check(load().fse_jacobian_apply_hypertime(self.h, _dp(a), _dp(out), k))
+        return out.reshape((self.N, 2 * self.n) if k == 1 else (k, self.N, 2 * self.n))
+
+    def newton_step_hypertime(self, zbar0, omega1):
+        """fse_newton_step_hypertime(): returns (updated zbar0, ||R_T||_2 before the update, rc)."""
+        zb = self._samples(zbar0, "zbar0")
+        rn = ctypes.c_double()
+        rc = load().fse_newton_step_hypertime(self.h, _dp(zb), float(omega1), ctypes.byref(rn))
+        self._check(rc, (FSE_ENOCONV,))
+        return zb, rn.value, rc
+
+    def set_rho(self, rho):
+        """fse_set_rho: the d-1 frequency ratios rho_j = w_{j+1} / w_1."""
+        r = _f64_vector(rho, self.d - 1, "rho")
+        self._check(load().fse_set_rho(self.h, _dp(r)))
+
+    def newton_step_unknown(self, Z0, omega1, rho, unknown):
+        """fse_newton_step_unknown: one Newton update of (Z(0), the unknown frequencies) at fixed w_1.
+        unknown: indices j (0-based, w_{j+2}) that are unknowns.  Returns (Z, rho, ||R||_2 before, rc)."""
+        Z = _f64_vector(Z0, self.n_unknowns, "Z0").copy()
+        r = _f64_vector(rho, self.d - 1, "rho").copy()
+        mask = np.zeros(self.d - 1, np.int32)
+        for j in unknown:
+            mask[int(j)] = 1
+        rn = ctypes.c_double()
+        rc = load().fse_newton_step_unknown(self.h, _dp(Z), float(omega1), _dp(r), _ip(mask), ctypes.byref(rn))
+        self._check(rc, (FSE_ENOCONV,))
+        return Z, r, rn.value, rc
+
+    def set_tangent_solve(self, kind="auto"):
+        """fse_set_tangent_solve: kind in {"auto", "simt", "tc"} (banded tangent-solve kernels)."""
+        k = {"auto": FSE_SOLVE_AUTO, "simt": FSE_SOLVE_SIMT, "tc": FSE_SOLVE_TC}[kind]
+        self._check(load().fse_set_tangent_solve(self.h, k))
 
     def linear_stats(self):
         """fse_linear_stats: (Krylov iterations, relative residual) of the last outer solve."""
