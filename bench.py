@@ -57,6 +57,8 @@ def parse():
                     help="converged continuation points of the plain FP64 form timed for the points/s "
                          "comparison (default: 1 when --points runs)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the GEMM peak measurements")
+    ap.add_argument("--solve", default="auto", choices=["auto", "simt", "tc"],
+                    help="banded tangent-solve kernels (fse_set_tangent_solve)")
     return ap.parse_args()
 
 
@@ -212,20 +214,20 @@ def step_work(m, N, band, ld, prec_bytes):
     }
 
 
-def kernel_source_hash():
-    """Hash of the tangent kernels' device code: fse_sens.cu up to its host launchers, plus the
-    device helpers of fse_common.cuh, with // comments and whitespace removed (a change in host
-    code or in a comment leaves it unchanged, any change of the device code does not)."""
+def kernel_source_hash(source="fse_sens.cu"):
+    """Hash of a kernel file's device code: the .cu file up to its host launchers, plus the device
+    helpers of fse_common.cuh, with // comments and whitespace removed (a change in host code or
+    in a comment leaves it unchanged, any change of the device code does not)."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2508_06302_gb300", "csrc")
-    dev = open(os.path.join(csrc, "fse_sens.cu")).read().split("// launchers", 1)[0]
+    dev = open(os.path.join(csrc, source)).read().split("// launchers", 1)[0]
     dev += open(os.path.join(csrc, "fse_common.cuh")).read()
     code = re.sub(r"\s+", "", re.sub(r"//[^\n]*", "", dev))
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload_name):
+def recorded_traffic(kernel, workload_name, source="fse_sens.cu"):
     """DRAM bytes per launch recorded by an ncu capture in profiles/, with the hash of the
     kernel sources it was taken on; None when absent or when the sources changed since."""
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload_name))
@@ -236,7 +238,7 @@ def recorded_traffic(kernel, workload_name):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             rec[k.strip()] = v.strip().strip("`")
-    h = kernel_source_hash()
+    h = kernel_source_hash(source)
     if rec.get("sources_sha256_16") != h:
         return None
     try:
@@ -480,6 +482,8 @@ def main():
     # every rank runs its own continuation point (weak scaling, no exchange)
     w1 = rank_omega(wl, rank)
     ctx = fse.Context.from_workload(wl, precision=args.precision, device=local)
+    if args.solve != "auto":
+        ctx.set_tangent_solve(args.solve)
     ctx.profile(True)
     n_newmark = wl.S1
     if 0 < args.newmark_steps < wl.S1:
@@ -565,6 +569,10 @@ def main():
     gkey = "fp32_simt_tflops" if wb == 4 else "fp64_tflops"
     alu_peak = peaks_gemm[gkey] if peaks_gemm else alu_derived
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # the banded solves run on the TF32 tensor cores (FP32 tangents, b <= 96): three TF32 products
+    # per FP32-accurate product, so their compute roof is a third of the measured TF32 GEMM rate
+    tc = wb == 4 and b <= 96 and args.solve == "tc"
+    tf32 = (peaks_gemm or {}).get("tf32_tflops") or 0.5 * peaks.get("bf16_tflops", 1900.0)
     kernels = {}
     for k_i, kname in enumerate(names):
         if kname not in work:
@@ -573,28 +581,42 @@ def main():
         if avg_ms <= 0:
             continue
         fl, by = work[kname]
-        t_alu = fl / (alu_peak * 1e12)
+        on_tc = tc and kname in ("sens_fwd", "sens_bwd")
+        cpeak = tf32 / 3.0 if on_tc else alu_peak
+        t_alu = fl / (cpeak * 1e12)
         t_hbm = by / (hbm_peak * 1e9)
         if t_alu >= t_hbm:
             ach = fl / (avg_ms / 1e3) / 1e12
-            kernels[kname] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                              "frac": ach / alu_peak, "avg_launch_ms": avg_ms,
+            kernels[kname] = {"bound": "tensor" if on_tc else "alu", "achieved": ach, "peak": cpeak,
+                              "unit": "TFLOP/s", "frac": ach / cpeak, "avg_launch_ms": avg_ms,
                               "algorithmic_flops": fl, "algorithmic_bytes": by}
         else:
             ach = by / (avg_ms / 1e3) / 1e9
             kernels[kname] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                               "frac": ach / hbm_peak, "avg_launch_ms": avg_ms,
                               "algorithmic_flops": fl, "algorithmic_bytes": by}
+        kernels[kname]["kernel"] = {"state": "k_state", "sens_rhs": "k_sens_rhs",
+                                    "sens_fwd": "k_tc_records + k_tc_solve<fwd>" if on_tc else "k_trsm8<fwd>",
+                                    "sens_bwd": "k_tc_solve<bwd>" if on_tc else "k_trsm8<bwd>"}[kname]
     roof = None
     if kernels:
         kname = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
         kk = kernels[kname]
-        roof = {"kernel": kname, "bound": kk["bound"], "achieved": kk["achieved"], "peak": kk["peak"],
-                "unit": kk["unit"], "frac": kk["frac"],
-                "traffic": recorded_traffic("k_" + kname, wl.name),
-                "peak_source": ("%s of %s (HBM copy)" % (hbm_peak, src)) if kk["bound"] == "hbm" else
-                (("measured cuBLAS %s GEMM (%s)" % ("FP32 TF32-off" if wb == 4 else "FP64", gkey)) if peaks_gemm
-                 else ("%d SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (n_sm, lanes, sm_mhz)))}
+        on_tc = tc and kname in ("sens_fwd", "sens_bwd")
+        tname = ("k_tc_solve_" + kname[5:]) if on_tc else ("k_" + kname)
+        if kk["bound"] == "hbm":
+            psrc = "%s of %s (HBM copy)" % (hbm_peak, src)
+        elif kk["bound"] == "tensor":
+            psrc = ("measured cuBLAS TF32 GEMM / 3 (three TF32 products per FP32-accurate product)" if peaks_gemm
+                    else "half the measured BF16 GEMM rate / 3")
+        elif peaks_gemm:
+            psrc = "measured cuBLAS %s GEMM (%s)" % ("FP32 TF32-off" if wb == 4 else "FP64", gkey)
+        else:
+            psrc = "%d SMs x %d lanes x 2 flop x median SM clock %.0f MHz (derived)" % (n_sm, lanes, sm_mhz)
+        roof = {"kernel": kname, "kernel_name": kk["kernel"], "bound": kk["bound"], "achieved": kk["achieved"],
+                "peak": kk["peak"], "unit": kk["unit"], "frac": kk["frac"],
+                "traffic": recorded_traffic(tname, wl.name, "fse_tc.cu" if on_tc else "fse_sens.cu"),
+                "peak_source": psrc}
     batch = None
     if args.batch:
         batch = batch_points(fse, local)
@@ -631,7 +653,8 @@ def main():
         "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
         # per evaluation: i-DFT, split, initial state, tangent init, S1 x (state step + the three
         # sensitivity kernels), join, DFT + residual
-        "gpu_launches": args.steps * (4 * n_newmark + 6),
+        # (+1 per step: the factor records of the tensor-core solves)
+        "gpu_launches": args.steps * ((5 if tc else 4) * n_newmark + 6),
         "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "peaks_source": src,
         "peaks_measured": peaks_gemm,
         "alu_peak_derived_tflops": alu_derived,

@@ -222,7 +222,8 @@ int fse_set_linear_solver(fse_ctx* ctx, int kind, double rel_tol, int restart, i
  * FSE_SOLVE_TC: the FP32 tangents on the TF32 tensor cores (tcgen05, accumulators in tensor
  * memory) with both operands split into a TF32 high part and an FP32 remainder and three
  * products per pair, which keeps FP32-level products; only for FSE_MIXED_FP32 contexts with
- * half-bandwidth b <= 96.  FSE_SOLVE_AUTO (default): FSE_SOLVE_TC where it applies, else SIMT.
+ * half-bandwidth b <= 96.  FSE_SOLVE_AUTO (default): the SIMT solves (measured faster on the
+ * 1872-dof shell, where the N = 32 tensor-core MMAs of the 32-row blocks are latency-bound).
  * Returns FSE_EINVAL for an unknown kind or FSE_SOLVE_TC where it does not apply. */
 #define FSE_SOLVE_AUTO 0
 #define FSE_SOLVE_SIMT 1

@@ -274,7 +274,9 @@ int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
 size_t tc_smem();
 void launch_tc_records(fse_ctx* c, int k, cudaStream_t st);
 void launch_tc_solve(fse_ctx* c, int phase, cudaStream_t st);
-inline bool use_tc(const fse_ctx* c) { return c->p.tc_ok && c->solve_kind != FSE_SOLVE_SIMT; }
+// FSE_SOLVE_AUTO keeps the SIMT solves: on the 1872-dof shell the tensor-core form measured slower
+// (N = 32 MMAs run at a third of the tensor rate and the block chain is latency-bound)
+inline bool use_tc(const fse_ctx* c) { return c->p.tc_ok && c->solve_kind == FSE_SOLVE_TC; }
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
 // same propagation with the static device scratch of fse_aft.cu (no allocation)
 int lyapunov_run_noalloc(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);

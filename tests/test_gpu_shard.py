@@ -101,6 +101,7 @@ def test_two_process_shards_on_one_gpu_match_the_unsharded_context():
     m = _model()
     w1 = 1.1 * m.omega_n1
     full = fse.Context(m, CASE["d"], CASE["S"], CASE["H"], CASE["rho"], CASE["S1"], newton_tol=0, newton_maxit=6)
+    full.set_linear_solver("gmres", rel_tol=1e-12, restart=60, max_iters=600)   # the shards' outer solver
     Z = I.random_coeffs(m.n, full.U, 1e-3, seed=3)
     V = I.random_coeffs(m.n, full.U, 1.0, seed=4)
     R, _, _, _ = full.residual_jacobian(Z, w1, True)
@@ -110,5 +111,5 @@ def test_two_process_shards_on_one_gpu_match_the_unsharded_context():
         Zn, rn, rc = full.newton_step(Zn, w1)
     assert np.abs(R0 - R).max() <= 1e-13 * np.abs(R).max()
     assert np.abs(J0 - JV).max() <= 1e-13 * np.abs(JV).max()
-    assert np.linalg.norm(Z0 - Zn) <= 1e-12 * np.linalg.norm(Zn)
+    assert np.linalg.norm(Z0 - Zn) <= 1e-11 * np.linalg.norm(Zn)
     full.close()
