@@ -222,8 +222,11 @@ int fse_set_linear_solver(fse_ctx* ctx, int kind, double rel_tol, int restart, i
  * FSE_SOLVE_TC: the FP32 tangents on the TF32 tensor cores (tcgen05, accumulators in tensor
  * memory) with both operands split into a TF32 high part and an FP32 remainder and three
  * products per pair, which keeps FP32-level products; only for FSE_MIXED_FP32 contexts with
- * half-bandwidth b <= 96.  FSE_SOLVE_AUTO (default): the SIMT solves (measured faster on the
- * 1872-dof shell, where the N = 32 tensor-core MMAs of the 32-row blocks are latency-bound).
+ * half-bandwidth b <= 96.  The tensor cores accumulate with truncation, so the TC tangents carry
+ * a biased error of a few FP32 ulps per block solve that grows along the period: about ten times
+ * the SIMT error on short periods, 1e-2 relative on the monodromy of the 1872-dof shell's
+ * 1000-step period, where Newton no longer converges quadratically.  FSE_SOLVE_AUTO (default):
+ * the SIMT solves.
  * Returns FSE_EINVAL for an unknown kind or FSE_SOLVE_TC where it does not apply. */
 #define FSE_SOLVE_AUTO 0
 #define FSE_SOLVE_SIMT 1

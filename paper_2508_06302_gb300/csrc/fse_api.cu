@@ -540,7 +540,7 @@ static int setup_impl(const fse_model* m, const fse_opts* o, long long s_begin, 
     A(&c->d.Rf, FSE_NBUF_F * rsz);
     A(&c->d.Rb, FSE_NBUF_F * rsz);
     if (p.tc_ok) {
-        const size_t tcsz = (size_t)N * (p.nblk + 1) * 8 * FSE_BLK * FSE_BLK * 4;
+        const size_t tcsz = (size_t)2 * N * (p.nblk + 1) * 8 * FSE_BLK * FSE_BLK * 4;   // two step parities
         A(&c->d.Tf, tcsz);
         A(&c->d.Tb, tcsz);
     }

@@ -101,9 +101,9 @@ struct Dev {
     // Rb = [L(i0 + 32 + c, i0 + r) at c * 32 + r | Dinv]; entries outside the band stay zero
     void* Rf = nullptr;
     void* Rb = nullptr;
-    // factor records of the tensor-core solves (FP32 tangents, b <= 96), per direction
-    // N x (nblk + 1) x 8192 floats: record sigma + 1 holds the four B operands (hi | lo, K-major)
-    // of the MMAs issued after block sigma (fse_tc.cu)
+    // factor records of the tensor-core solves (FP32 tangents, b <= 96), per direction two
+    // buffers (step parity) of N x (nblk + 1) x 8192 floats: record sigma + 1 holds the B operands
+    // (hi | lo, K-major) of the MMAs issued after block sigma (fse_tc.cu)
     void* Tf = nullptr;
     void* Tb = nullptr;
     // tangents (sensitivity precision)
@@ -269,13 +269,14 @@ void launch_dense_jac_ht(fse_ctx* c, const double* Pm, double* J);
 // (m + 1) x (m + 1) pseudo-arclength matrix [J dR/dw_1; t_Z^T tail] (row-major)
 void launch_bordered_jac(fse_ctx* c, const double* Rw, const double* tZ, double tail, double* B);
 int dense_lu_solve(fse_ctx* c, double* A, double* bvec, int m);
-// tensor-core tangent solves (fse_tc.cu): dynamic shared memory, per-step factor records (both
-// directions, from the factor of step k) and the forward (phase 1) / backward (phase 2) solve
-size_t tc_smem();
+// tensor-core tangent solves (fse_tc.cu): per-step factor records of both directions from the
+// factor of step k (record buffer k % 2, launched on the state stream right after state step k)
+// and the forward (phase 1) / backward (phase 2) solve of step k
 void launch_tc_records(fse_ctx* c, int k, cudaStream_t st);
-void launch_tc_solve(fse_ctx* c, int phase, cudaStream_t st);
-// FSE_SOLVE_AUTO keeps the SIMT solves: on the 1872-dof shell the tensor-core form measured slower
-// (N = 32 MMAs run at a third of the tensor rate and the block chain is latency-bound)
+void launch_tc_solve(fse_ctx* c, int k, int phase, cudaStream_t st);
+// FSE_SOLVE_AUTO keeps the SIMT solves: the tensor cores' truncating FP32 accumulation makes the
+// tangents of a long period drift (on the 1872-dof shell the monodromy of a 1000-step period
+// differs from the SIMT one by 1e-2, enough to stall Newton's convergence)
 inline bool use_tc(const fse_ctx* c) { return c->p.tc_ok && c->solve_kind == FSE_SOLVE_TC; }
 int lyapunov_run(fse_ctx* c, double omega1, int N_Ly, int h, double* sigma);
 // same propagation with the static device scratch of fse_aft.cu (no allocation)

@@ -1037,8 +1037,7 @@ void launch_sens_phase(fse_ctx* c, int k, double w, int phase, cudaStream_t st) 
         return;
     }
     if (phase > 0 && use_tc(c)) {
-        if (phase == 1) launch_tc_records(c, k, st);
-        launch_tc_solve(c, phase, st);
+        launch_tc_solve(c, k, phase, st);
         return;
     }
     if (p.prec == FSE_MIXED_FP32)

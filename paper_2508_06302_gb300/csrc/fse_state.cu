@@ -986,6 +986,9 @@ void launch_state_step(fse_ctx* c, int k, double w, cudaStream_t st, bool sens) 
         state_launch<float>(c, A, st);
     else
         state_launch<double>(c, A, st);
+    // the tensor-core solves of step k read records built from this step's factor: built here, on the
+    // state stream, so that they overlap the tangent kernels of step k - 1 (record buffer k % 2)
+    if (sens && use_tc(c)) launch_tc_records(c, k, st);
 }
 
 }  // namespace fse

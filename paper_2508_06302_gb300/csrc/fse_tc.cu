@@ -15,15 +15,23 @@
 // accumulation (the dropped a_lo b_lo is 2^-22 relative).
 //
 // One CTA solves 128 tangent columns of one trajectory.  The MMA is D[m][r] += sum_k
-// A[m][k] B[r][k] with M = 128 (tangent columns, TMEM lanes), N = 32 (rows of the target
-// block, TMEM columns) and K = 32 (rows of the source block), kind::tf32, both operands
-// K-major in shared memory without swizzle.  Four accumulators of 32 TMEM columns rotate over
-// the blocks.  Roles: warps 0-3 (epilogue, thread m = column m) read a finished block out of
-// TMEM, store it, stage it as the A operand of later blocks and stage the right-hand side of
-// the block two ahead; warp 4 (one thread) issues the MMAs; warp 5 (one thread) streams the
-// factor records with bulk copies.  After block q is read out ("round q") the MMA thread issues
-//   1. the critical term of block q+1: G(q+1, q) Y'_q, then commits block q+1;
-//   2. the right-hand-side term Dinv_{q+2} Y_{q+2} and the terms G(q+2, q) Y'_q, G(q+3, q) Y'_q.
+// A[m][k] B[r][k] with M = 128 (tangent columns, TMEM lanes), K = 32 (rows of the source block)
+// and N = 32 rows per target block, kind::tf32.  A (the solved block or a right-hand side, split
+// hi/lo) lives in tensor memory, written by the epilogue with tcgen05.st; B (the factor couplings)
+// is K-major in shared memory without swizzle.  With A in shared memory the small-N MMAs were
+// bound by shared-memory bandwidth (an M = 128, K = 8 A tile is 4 KB per MMA); from tensor memory
+// the tensor core reads only B there.  Eight accumulators of 32 TMEM columns rotate over the blocks (block t in columns
+// 32 (t mod 8)), so the three blocks a solved block feeds are adjacent: one MMA of N = 96 pushes
+// a source block into all of them (N = 32 MMAs run at a third of the tensor rate, N >= 96 at
+// two thirds or more; the push splits in two where the ring wraps).  Roles: the epilogue warps
+// read a finished block out of TMEM, stage it as the A operand (in TMEM), stage the
+// right-hand side three blocks ahead (loaded into registers one block earlier) and store the
+// block; warps 0-15 share this (thread = one column, 8 of the 32 rows of each block, so four
+// warps per TMEM lane quarter), with the next block's loads in flight in register double
+// buffers; warp 16 (one thread) issues the MMAs; warp 17 (one thread) streams the factor records
+// with bulk copies.  After block q is read out ("round q") the MMA thread issues
+//   1. the push of Y'_q into blocks q+1 .. q+ND, then commits block q+1;
+//   2. the right-hand-side term Dinv'_{q+3} Y_{q+3} of block q+3.
 // The accumulators are zeroed by the epilogue after each read-out, so every MMA accumulates.
 // Every wait is bounded (about 2 s of SM clock); a wait that gives up raises the context's
 // error flag, the CTA drains its MMAs and copies in flight, frees its tensor memory and exits.
@@ -35,12 +43,24 @@ namespace fse {
 
 constexpr int TC_M = 128;                       // tangent columns per CTA (MMA M, TMEM lanes)
 constexpr int TC_MAT = FSE_BLK * FSE_BLK;       // floats of one 32 x 32 operand
-constexpr int TC_REC = 8 * TC_MAT;              // floats of one record: 4 operands x (hi, lo)
+constexpr int TC_CPL = 3 * TC_MAT;              // floats of the 96-row coupling operand (hi or lo)
+constexpr int TC_REC = 2 * TC_CPL + 2 * TC_MAT; // floats of one record: couplings (hi, lo), D' (hi, lo)
 constexpr int TC_AOP = TC_M * FSE_BLK;          // floats of one 128 x 32 A operand (hi or lo)
 constexpr int TC_NREC = 3;                      // record slots in shared memory
-constexpr unsigned TC_SMEM = (unsigned)((2 * 2 + 2 * 2) * TC_AOP + TC_NREC * TC_REC) * 4u;
-constexpr unsigned TC_TMEM_COLS = 128;          // 4 accumulators x 32 columns
-constexpr int TC_THREADS = 192;
+constexpr int TC_NACC = 8;                      // accumulators of 32 TMEM columns
+// shared memory holds only the record slots (both A operands live in tensor memory); the launch
+// asks for more than half of an SM's shared memory so that no second CTA, which would block in
+// tcgen05.alloc until this one frees its 512 TMEM columns, is placed on the same SM
+constexpr unsigned TC_SMEM_USED = (unsigned)(TC_NREC * TC_REC) * 4u;
+constexpr unsigned TC_SMEM = 116u * 1024u;
+static_assert(TC_SMEM >= TC_SMEM_USED, "record slots exceed the launch's shared memory");
+// tensor memory columns: 8 accumulators (0..255), the solved block's A operand hi | lo (256..319),
+// two right-hand-side A operands hi | lo (320..447)
+constexpr unsigned TC_COL_A = 32 * TC_NACC;
+constexpr unsigned TC_COL_RHS = TC_COL_A + 64;
+constexpr unsigned TC_TMEM_COLS = 512;
+constexpr int TC_EPI = 512;                     // epilogue threads: 16 warps, four per TMEM lane quarter
+constexpr int TC_THREADS = TC_EPI + 64;         // + the MMA warp and the record warp
 
 // Byte offset of element (row, k), k < 32, of a K-major operand in the no-swizzle canonical
 // layout: 8 rows x 16 bytes per core matrix, K-adjacent core matrices 128 bytes apart (the
@@ -56,14 +76,16 @@ __device__ __forceinline__ unsigned long long tc_desc(unsigned addr) {
            ((unsigned long long)(1024u >> 4) << 32) | (1ull << 46);
 }
 
-// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, N = 32, M = 128
-constexpr unsigned TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M = 128, N = nrows
+__host__ __device__ constexpr unsigned tc_idesc(int nrows) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(nrows >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-__device__ __forceinline__ void tc_mma(unsigned dtm, unsigned long long ad, unsigned long long bd) {
+__device__ __forceinline__ void tc_mma(unsigned dtm, unsigned long long ad, unsigned long long bd, unsigned idesc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %4, p;\n}\n" ::"r"(dtm),
-        "l"(ad), "l"(bd), "r"(1), "r"(TC_IDESC)
+        "l"(ad), "l"(bd), "r"(1), "r"(idesc)
         : "memory");
 }
 __device__ __forceinline__ void tc_commit(unsigned long long* bar) {
@@ -75,40 +97,35 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// 32 consecutive TMEM columns of this thread's lane (warp w reads lanes 32 (w % 4) ..)
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, float v[32]) {
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+// TC_HR consecutive TMEM columns of this thread's lane (warp w reads lanes 32 (w % 4) ..)
+constexpr int TC_HR = 8;    // rows of a block per epilogue thread (four warps per TMEM lane quarter)
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float v[TC_HR]) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-// zero 32 consecutive TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_zero32(unsigned taddr) {
+// zero 8 consecutive TMEM columns of this thread's lane (completion waited for by the caller's
+// tcgen05.wait::st before its next thread synchronisation)
+__device__ __forceinline__ void tmem_zero8(unsigned taddr) {
     const unsigned z = 0u;
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};\n" ::"r"(taddr),
-        "r"(z)
-        : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};\n" ::"r"(taddr),
+                 "r"(z)
+                 : "memory");
 }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // TF32 split: hi exact in TF32 (13 low mantissa bits cleared), lo = x - hi exact in FP32
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// rows 32 B .. 32 B + 31 of column t of a tangent-sized array (zero outside)
-__device__ __forceinline__ void load_col32(const float* base, int B, int n, int ld, int t, float v[32]) {
+// rows 32 B + r0 .. 32 B + r0 + 7 of column t of a tangent-sized array (zero outside)
+__device__ __forceinline__ void load_rows8(const float* base, int B, int r0, int n, int ld, int t, float v[TC_HR]) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        const int i = B * FSE_BLK + r;
+    for (int r = 0; r < TC_HR; ++r) {
+        const int i = B * FSE_BLK + r0 + r;
         v[r] = (i < n && t < ld) ? __ldcs(base + (size_t)i * ld + t) : 0.0f;
     }
 }
@@ -123,37 +140,44 @@ __device__ __forceinline__ void prefetch_rows32(const float* base, int B, int n,
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a + min(31, ld - 1 - t0w)));
 }
 
-// this thread's row m of a 128 x 32 A operand (hi at sA, lo at sA + TC_AOP floats)
-__device__ __forceinline__ void stage_row(unsigned sA, int m, const float v[32]) {
+// D (nrows TMEM columns at dtm) += A B^T with A (128 x 32) in tensor memory (hi in the 32 columns
+// at ahi, lo in the 32 at ahi + 32: lane m = row m, column k = K index k) and B (nrows x 32) in
+// shared memory (hi at sB, lo at sB + lo_off bytes): per K step of 8, the three split products,
+// small ones first
+__device__ __forceinline__ void tc_mma_ts(unsigned dtm, unsigned atm, unsigned long long bd, unsigned idesc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %4, p;\n}\n" ::"r"(dtm),
+        "r"(atm), "l"(bd), "r"(1), "r"(idesc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_k32(unsigned dtm, unsigned ahi, unsigned sB, unsigned lo_off, int nrows) {
+    const unsigned idesc = tc_idesc(nrows);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        float h[4], l[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            h[j] = tf32_hi(v[4 * c + j]);
-            l[j] = v[4 * c + j] - h[j];
-        }
-        const unsigned o = kmaj_off(m, 4 * c);
-        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(sA + o), "f"(h[0]), "f"(h[1]), "f"(h[2]),
-                     "f"(h[3])
-                     : "memory");
-        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(sA + TC_AOP * 4u + o), "f"(l[0]), "f"(l[1]),
-                     "f"(l[2]), "f"(l[3])
-                     : "memory");
+    for (int kk = 0; kk < 4; ++kk) {
+        const unsigned long long bh = tc_desc(sB + kk * 256u), bl = tc_desc(sB + lo_off + kk * 256u);
+        tc_mma_ts(dtm, ahi + 32 + 8 * kk, bh, idesc);
+        tc_mma_ts(dtm, ahi + 8 * kk, bl, idesc);
+        tc_mma_ts(dtm, ahi + 8 * kk, bh, idesc);
     }
 }
 
-// D (32 TMEM columns at dtm) += A (128 x 32, hi at sA, lo at sA + 16 KB) B^T (B 32 x 32, hi at sB,
-// lo at sB + 4 KB): per K step of 8, the three split products, small ones first
-__device__ __forceinline__ void mma_k32(unsigned dtm, unsigned sA, unsigned sB) {
+// this thread's 8 K values (rows r0 .. r0 + 7 of the block, A row m = its TMEM lane) split into hi
+// and lo and written to TMEM columns col .. col + 7 (hi) and col + 32 .. (lo) of its lane (taddr =
+// lane quarter + col + r0); completion is waited for by the caller's tcgen05.wait::st
+__device__ __forceinline__ void tmem_stage8(unsigned taddr, const float v[TC_HR]) {
+    float h[8], l[8];
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const unsigned long long ah = tc_desc(sA + kk * 256u), al = tc_desc(sA + TC_AOP * 4u + kk * 256u);
-        const unsigned long long bh = tc_desc(sB + kk * 256u), bl = tc_desc(sB + TC_MAT * 4u + kk * 256u);
-        tc_mma(dtm, al, bh);
-        tc_mma(dtm, ah, bl);
-        tc_mma(dtm, ah, bh);
+    for (int j = 0; j < 8; ++j) {
+        h[j] = tf32_hi(v[j]);
+        l[j] = v[j] - h[j];
     }
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+                 "f"(h[0]), "f"(h[1]), "f"(h[2]), "f"(h[3]), "f"(h[4]), "f"(h[5]), "f"(h[6]), "f"(h[7])
+                 : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr + 32u),
+                 "f"(l[0]), "f"(l[1]), "f"(l[2]), "f"(l[3]), "f"(l[4]), "f"(l[5]), "f"(l[6]), "f"(l[7])
+                 : "memory");
 }
 
 struct TcArgs {
@@ -170,16 +194,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs A) {
     const int s = blockIdx.y, t0 = blockIdx.x * TC_M;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ __align__(128) unsigned char smraw[];
-    // A operands of the last two solved blocks [2][hi | lo], staged right-hand sides [2][hi | lo],
-    // factor records [3]
-    const unsigned sAop = smem_addr(smraw);
-    const unsigned sRhs = sAop + 2u * 2u * TC_AOP * 4u;
-    const unsigned sRec = sRhs + 2u * 2u * TC_AOP * 4u;
-    float* recs = reinterpret_cast<float*>(smraw + (size_t)8 * TC_AOP * 4);
-    // rhs_ready[a & 1] completes arrival a of the staged right-hand sides (a = 0: blocks 0 and 1 in the
-    // prologue, a = q + 1: block q + 2 in round q); two barriers so that the MMA thread, which waits
-    // for arrival a after committing block q + 1, can never see arrival a + 2 on the same barrier first
-    __shared__ __align__(8) unsigned long long acc_full[4], rec_full[TC_NREC], epi_done, rhs_ready[2], drain;
+    // A operand of the last solved block [hi | lo], staged right-hand sides [2][hi | lo], records [3]
+    const unsigned sRec = smem_addr(smraw);
+    float* recs = reinterpret_cast<float*>(smraw);
+    const unsigned recb = (unsigned)TC_REC * 4u;
+    const unsigned cpl_lo = (unsigned)TC_CPL * 4u;           // lo part of the coupling operand
+    const unsigned dsl = 2u * TC_CPL * 4u, dsl_lo = (unsigned)TC_MAT * 4u;   // D' operand, its lo part
+    // rhs_ready[a & 1] completes arrival a of the staged right-hand sides: a = 0 blocks 0 and 1
+    // (prologue), a = 1 block 2 (prologue), a = q + 2 block q + 3 (round q).  The MMA thread waits
+    // for arrival a before the epilogue can start arrival a + 2 on the same barrier.
+    __shared__ __align__(8) unsigned long long acc_full[TC_NACC], rec_full[TC_NREC], epi_done, rhs_ready[2],
+        rhs_free, drain;
     __shared__ unsigned s_taddr;
     __shared__ volatile int s_abort;
     const size_t base = (size_t)s * n * ld;
@@ -188,17 +213,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs A) {
     float* V = A.V + base;
     const float* R = A.rec + (size_t)s * (nblk + 1) * TC_REC;
     auto blk = [&](int q) { return FWD ? q : nblk - 1 - q; };
+    // TMEM column of the right-hand-side A operand of block t (hi; lo 32 columns further)
+    auto rhs_slot = [&](int t) { return TC_COL_RHS + (unsigned)(t & 1) * 64u; };
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 4; ++k) mbar_init(&acc_full[k], 1);
+        for (int k = 0; k < TC_NACC; ++k) mbar_init(&acc_full[k], 1);
         for (int k = 0; k < TC_NREC; ++k) mbar_init(&rec_full[k], 1);
-        mbar_init(&epi_done, 128);
-        mbar_init(&rhs_ready[0], 128);
-        mbar_init(&rhs_ready[1], 128);
+        mbar_init(&epi_done, TC_EPI);
+        mbar_init(&rhs_ready[0], TC_EPI);
+        mbar_init(&rhs_ready[1], TC_EPI);
+        mbar_init(&rhs_free, 1);
         mbar_init(&drain, 1);
         s_abort = 0;
         mbar_fence_init();
     }
-    if (warp == 4) {
+    if (warp == 16) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&s_taddr)),
                      "r"(TC_TMEM_COLS)
                      : "memory");
@@ -208,87 +236,120 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs A) {
     __syncthreads();
     tc_fence_after();
     const unsigned tbase = s_taddr;
-    const unsigned recb = (unsigned)TC_REC * 4u;
 
-    if (warp < 4) {
-        // ---------------- epilogue: thread m = column t0 + m, TMEM lane m
-        const int m = threadIdx.x, t = t0 + m;
-        const unsigned tl = tbase + ((unsigned)(warp * 32) << 16);
-        for (int a = 0; a < 4; ++a) tmem_zero32(tl + a * 32);
-        float rhs[32];
-        load_col32(Y, blk(0), n, ld, t, rhs);
-        stage_row(sRhs, m, rhs);
+    if (warp < 16) {
+        // ---------------- epilogue: thread (warp w, lane l) = column t0 + m, m = 32 (w % 4) + l (TMEM
+        // lane m), rows r0 .. r0 + 7 of each block, r0 = 8 (w / 4)
+        const int m = (warp & 3) * 32 + lane, r0 = (warp >> 2) * TC_HR, t = t0 + m;
+        const int t0w = t0 + (warp & 3) * 32;
+        const bool pf = warp < 4;                  // one warp of each lane quarter issues the L2 prefetches
+        const unsigned tl = tbase + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)r0;
+        for (int a = 0; a < TC_NACC; ++a) tmem_zero8(tl + a * 32);
+        tmem_wait_st();
+        // register double buffers: right-hand side three blocks ahead, backward X_k and V_k of the block
+        float rA[TC_HR], rB[TC_HR], xA[TC_HR], xB[TC_HR], vA[TC_HR], vB[TC_HR];
+        load_rows8(Y, blk(0), r0, n, ld, t, rA);
+        tmem_stage8(tl + rhs_slot(0), rA);
         if (nblk > 1) {
-            load_col32(Y, blk(1), n, ld, t, rhs);
-            stage_row(sRhs + 2u * TC_AOP * 4u, m, rhs);
+            load_rows8(Y, blk(1), r0, n, ld, t, rA);
+            tmem_stage8(tl + rhs_slot(1), rA);
         }
-        fence_async_smem();
+        tmem_wait_st();
         tc_fence_before();
-        mbar_arrive(&rhs_ready[0]);
-        const int t0w = t0 + warp * 32;
-        for (int q = 2; q < 5 && q < nblk; ++q) prefetch_rows32(Y, blk(q), n, ld, t0w);
-        if (!FWD)
-            for (int q = 0; q < 3 && q < nblk; ++q) {
-                prefetch_rows32(X, blk(q), n, ld, t0w);
-                prefetch_rows32(V, blk(q), n, ld, t0w);
-            }
-        for (int q = 0; q < nblk; ++q) {
+        mbar_arrive(&rhs_ready[0]);                       // arrival 0
+        if (nblk > 2) load_rows8(Y, blk(2), r0, n, ld, t, rA);
+        if (pf) {
+            for (int q = 3; q < 6 && q < nblk; ++q) prefetch_rows32(Y, blk(q), n, ld, t0w);
+            if (!FWD)
+                for (int q = 0; q < 3 && q < nblk; ++q) {
+                    prefetch_rows32(X, blk(q), n, ld, t0w);
+                    prefetch_rows32(V, blk(q), n, ld, t0w);
+                }
+        }
+        // block 2's right-hand side goes into slot 0 once the MMAs of blocks 0 and 1 have read it
+        if (!mbar_wait(&rhs_free, 0, A.err)) s_abort = 1;
+        tc_fence_after();
+        if (nblk > 2) tmem_stage8(tl + rhs_slot(2), rA);
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&rhs_ready[1]);                       // arrival 1
+        if (nblk > 3) load_rows8(Y, blk(3), r0, n, ld, t, rA);
+        if (!FWD) {
+            load_rows8(X, blk(0), r0, n, ld, t, xA);
+            load_rows8(V, blk(0), r0, n, ld, t, vA);
+        }
+        // one block: rc holds the right-hand side of block q + 3 and xc, vc the backward X_k, V_k of
+        // block q; the next block's are loaded into rn, xn, vn here and used one block later
+        auto round = [&](int q, float (&rc)[TC_HR], float (&rn)[TC_HR], float (&xc)[TC_HR], float (&vc)[TC_HR],
+                         float (&xn)[TC_HR], float (&vn)[TC_HR]) -> bool {
             const int B = blk(q);
-            const bool more = q + 2 < nblk;
-            // L2 prefetch three blocks ahead of the loads below: right-hand side rows of block q + 5,
-            // backward X_k and V_k rows of block q + 3
-            if (q + 5 < nblk) prefetch_rows32(Y, blk(q + 5), n, ld, t0w);
-            if (!FWD && q + 3 < nblk) {
-                prefetch_rows32(X, blk(q + 3), n, ld, t0w);
-                prefetch_rows32(V, blk(q + 3), n, ld, t0w);
+            if (q + 4 < nblk) load_rows8(Y, blk(q + 4), r0, n, ld, t, rn);
+            if (pf && q + 6 < nblk) prefetch_rows32(Y, blk(q + 6), n, ld, t0w);
+            if (!FWD && q + 1 < nblk) {
+                if (pf && q + 3 < nblk) {
+                    prefetch_rows32(X, blk(q + 3), n, ld, t0w);
+                    prefetch_rows32(V, blk(q + 3), n, ld, t0w);
+                }
+                load_rows8(X, blk(q + 1), r0, n, ld, t, xn);
+                load_rows8(V, blk(q + 1), r0, n, ld, t, vn);
             }
-            if (more) load_col32(Y, blk(q + 2), n, ld, t, rhs);
-            float xo[32], vo[32];
-            if (!FWD) {
-                load_col32(X, B, n, ld, t, xo);
-                load_col32(V, B, n, ld, t, vo);
-            }
-            if (s_abort || !mbar_wait(&acc_full[q & 3], (q >> 2) & 1, A.err)) {
+            if (s_abort || !mbar_wait(&acc_full[q & 7], (q >> 3) & 1, A.err)) {
                 s_abort = 1;
-                break;
+                return false;
             }
             tc_fence_after();
-            float y[32];
-            tmem_ld32(tl + (q & 3) * 32, y);
-            tmem_zero32(tl + (q & 3) * 32);   // ready for block q + 4
-            stage_row(sAop + (unsigned)(q & 1) * 2u * TC_AOP * 4u, m, y);
-            fence_async_smem();
+            float y[TC_HR];
+            tmem_ld8(tl + (q & 7) * 32, y);
+            tmem_stage8(tl + TC_COL_A, y);
+            tmem_wait_st();
             tc_fence_before();
             mbar_arrive(&epi_done);
+            // off the critical path: zero the accumulator for block q + 8, stage the right-hand side of
+            // block q + 3 (its slot's previous block, q + 1, was read by round q - 2, finished before
+            // block q was committed)
+            tmem_zero8(tl + (q & 7) * 32);
+            if (q + 3 < nblk) tmem_stage8(tl + rhs_slot(q + 3), rc);
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&rhs_ready[q & 1]);               // arrival q + 2
             if (t < ld) {
 #pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    const int i = B * FSE_BLK + r;
+                for (int r = 0; r < TC_HR; ++r) {
+                    const int i = B * FSE_BLK + r0 + r;
                     if (i < n) {
                         const size_t o = (size_t)i * ld + t;
                         if (FWD) {
                             __stcs(Y + o, y[r]);
                         } else {
                             __stcs(X + o, y[r]);
-                            __stcs(V + o, A.a2c * (y[r] - xo[r]) - vo[r]);
+                            __stcs(V + o, A.a2c * (y[r] - xc[r]) - vc[r]);
                         }
                     }
                 }
             }
-            if (more) stage_row(sRhs + (unsigned)(q & 1) * 2u * TC_AOP * 4u, m, rhs);
-            fence_async_smem();
-            mbar_arrive(&rhs_ready[(q + 1) & 1]);
+            return true;
+        };
+        for (int q = 0; q < nblk; q += 2) {
+            if (!round(q, rA, rB, xA, vA, xB, vB)) break;
+            if (q + 1 < nblk && !round(q + 1, rB, rA, xB, vB, xA, vA)) break;
         }
-    } else if (warp == 4) {
+    } else if (warp == 16) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
             bool ok = mbar_wait(&rec_full[0], 0, A.err) && mbar_wait(&rhs_ready[0], 0, A.err);
             if (ok) {
+                // prologue: right-hand-side terms of blocks 0, 1 (slots 0, 1), then 2 (slot 0 again);
+                // record 0 holds D'_0, D'_1, D'_2 as rows 0-31, 32-63, 64-95 of its coupling operand
                 tc_fence_after();
-                // round -1: the right-hand-side terms of blocks 0 and 1 (record 0: Dinv'_0, Dinv'_1)
-                mma_k32(tbase + 0, sRhs, sRec);
-                tc_commit(&acc_full[0]);
-                if (nblk > 1) mma_k32(tbase + 32, sRhs + 2u * TC_AOP * 4u, sRec + 2u * TC_MAT * 4u);
+                mma_k32(tbase + 0, tbase + rhs_slot(0), sRec, cpl_lo, 32);
+                if (nblk > 1) mma_k32(tbase + 32, tbase + rhs_slot(1), sRec + 4096u, cpl_lo, 32);
+                tc_commit(&rhs_free);
+                ok = mbar_wait(&rhs_ready[1], 0, A.err);
+                if (ok) {
+                    tc_fence_after();
+                    if (nblk > 2) mma_k32(tbase + 64, tbase + rhs_slot(2), sRec + 8192u, cpl_lo, 32);
+                    tc_commit(&acc_full[0]);
+                }
             }
             for (int q = 0; ok && q < nblk; ++q) {
                 if (s_abort || !mbar_wait(&epi_done, q & 1, A.err)) {
@@ -302,23 +363,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs A) {
                     break;
                 }
                 tc_fence_after();
-                const unsigned sA = sAop + (unsigned)(q & 1) * 2u * TC_AOP * 4u;
                 const unsigned sB = sRec + (unsigned)rs * recb;
-                // record q + 1: [-G(q+1, q), -G(q+2, q), -G(q+3, q), Dinv'_{q+2}], each hi | lo
-                if (ND >= 1) mma_k32(tbase + ((q + 1) & 3) * 32, sA, sB);
-                tc_commit(&acc_full[(q + 1) & 3]);
-                // arrival q + 1 (right-hand side of block q + 2 staged by the epilogue of block q)
-                if (!mbar_wait(&rhs_ready[(q + 1) & 1], ((q + 1) >> 1) & 1, A.err)) {
+                // record q + 1: couplings C(q+1, q), C(q+2, q), C(q+3, q) as rows 0-95, then D'(q+3)
+                const int nt = min(ND, nblk - 1 - q);          // blocks this one feeds
+                if (nt > 0) {
+                    const int a0 = (q + 1) & 7, n1 = min(nt, TC_NACC - a0);
+                    mma_k32(tbase + a0 * 32, tbase + TC_COL_A, sB, cpl_lo, 32 * n1);
+                    if (n1 < nt) mma_k32(tbase, tbase + TC_COL_A, sB + (unsigned)n1 * 4096u, cpl_lo, 32 * (nt - n1));
+                }
+                tc_commit(&acc_full[(q + 1) & 7]);
+                // arrival q + 2: the right-hand side of block q + 3 is staged
+                if (!mbar_wait(&rhs_ready[q & 1], ((q + 2) >> 1) & 1, A.err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                if (q + 2 < nblk) {
-                    mma_k32(tbase + ((q + 2) & 3) * 32, sRhs + (unsigned)(q & 1) * 2u * TC_AOP * 4u,
-                            sB + 6u * TC_MAT * 4u);
-                    if (ND >= 2) mma_k32(tbase + ((q + 2) & 3) * 32, sA, sB + 2u * TC_MAT * 4u);
-                }
-                if (ND >= 3 && q + 3 < nblk) mma_k32(tbase + ((q + 3) & 3) * 32, sA, sB + 4u * TC_MAT * 4u);
+                if (q + 3 < nblk) mma_k32(tbase + ((q + 3) & 7) * 32, tbase + rhs_slot(q + 3), sB + dsl, dsl_lo, 32);
             }
             if (!ok) s_abort = 1;
             // every MMA issued has finished before the tensor memory is released
@@ -334,10 +394,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs A) {
                 bulk_g2s(recs + (size_t)r * TC_REC, R + (size_t)r * TC_REC, recb, &rec_full[r]);
                 issued = r + 1;
             }
-            // record q + 3 (round q + 2) replaces record q once block q + 1 is committed, which
-            // implies that every MMA of round q - 1 (the last reader of record q) has finished
+            // record q + 3 (round q + 2) replaces record q (round q - 1) once block q + 1 is committed:
+            // that commit follows every MMA of round q - 1
             for (int q = 0; q + 3 < nblk; ++q) {
-                if (s_abort || !mbar_wait(&acc_full[(q + 1) & 3], ((q + 1) >> 2) & 1, A.err)) {
+                if (s_abort || !mbar_wait(&acc_full[(q + 1) & 7], ((q + 1) >> 3) & 1, A.err)) {
                     s_abort = 1;
                     break;
                 }
@@ -354,17 +414,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs A) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 4)
+    if (warp == 16)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TC_TMEM_COLS)
                      : "memory");
 }
 
 // Factor records of both directions for the tensor-core solves, one CTA per (target block in
 // processing order tau, trajectory, direction).  Processing order: forward blocks 0, 1, ..;
-// backward blocks nblk-1, nblk-2, ...  Record sigma + 1 holds the B operands of round sigma:
-//   [-C(sigma+1, sigma), -C(sigma+2, sigma), -C(sigma+3, sigma), D'(sigma+2)],
-// record 0 holds [D'(0), D'(1), -, -], each as hi | lo in the K-major layout (element (r, k) =
-// B[r][k], r the row of the target block, k the row of the source block).
+// backward blocks nblk-1, nblk-2, ...  Record sigma + 1 holds the B operands of round sigma: the
+// 96-row coupling operand [-C(sigma+1, sigma); -C(sigma+2, sigma); -C(sigma+3, sigma)] and
+// D'(sigma+3); record 0 holds [D'(0); D'(1); D'(2)] in its coupling operand.  Each operand as
+// hi | lo in the K-major layout (element (r, k) = B[r][k], r the row of the target block, k the
+// row of the source block).
 //   forward:  C(t, s)[r][k] = sum_j Dinv_t[r][j] L(32 t + j, 32 s + k),     D'(t) = Dinv_t
 //   backward: C(t, s)[r][k] = sum_j Dinv_t[j][r] L(32 s + k, 32 t + j),     D'(t) = Dinv_t^T
 // (t, s block indices of the processing positions; the rows and columns past n are zero, the
@@ -386,18 +447,21 @@ __global__ void __launch_bounds__(256) k_tc_records(int n, int b, int nblk, int 
     auto L = [&](int i, int j) -> float {
         return (i < n && j >= 0 && j <= i && i - j <= b) ? Lband[(size_t)i * nb + (j - i + b)] : 0.0f;
     };
-    auto put = [&](int rho, int slot, int r, int k, float v) {
-        float* m = rec + (size_t)rho * TC_REC + (size_t)slot * 2 * TC_MAT;
+    // element (r, k) of an operand whose hi part starts at float offset o0 (lo at o0 + lo)
+    auto put = [&](size_t o0, size_t lo, int r, int k, float v) {
         const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-        const unsigned o = kmaj_off(r, k) / 4u;
-        m[o] = h;
-        m[TC_MAT + o] = v - h;
+        const size_t o = o0 + kmaj_off(r, k) / 4u;
+        rec[o] = h;
+        rec[o + lo] = v - h;
     };
-    {   // D'(tau)
-        const int rho = tau >= 2 ? tau - 1 : 0, slot = tau >= 2 ? 3 : tau;
+    {   // D'(tau): record 0 rows 32 tau.. of the coupling operand (tau <= 2), else record tau - 2's D'
         for (int x = threadIdx.x; x < TC_MAT; x += blockDim.x) {
             const int r = x >> 5, k = x & 31;
-            put(rho, slot, r, k, fwd ? Dv[r][k] : Dv[k][r]);
+            const float v = fwd ? Dv[r][k] : Dv[k][r];
+            if (tau <= 2)
+                put(0, TC_CPL, 32 * tau + r, k, v);
+            else
+                put((size_t)(tau - 2) * TC_REC + 2 * TC_CPL, TC_MAT, r, k, v);
         }
     }
     for (int u = 1; u <= ND; ++u) {
@@ -416,7 +480,7 @@ __global__ void __launch_bounds__(256) k_tc_records(int n, int b, int nblk, int 
             float acc = 0.0f;
 #pragma unroll 8
             for (int j = 0; j < 32; ++j) acc = fmaf(fwd ? Dv[r][j] : Dv[j][r], Lt[j][k], acc);
-            put(sig + 1, u - 1, r, k, -acc);
+            put((size_t)(sig + 1) * TC_REC, TC_CPL, 32 * (u - 1) + r, k, -acc);
         }
     }
 }
@@ -425,7 +489,8 @@ __global__ void __launch_bounds__(256) k_tc_records(int n, int b, int nblk, int 
 // launchers
 // ----------------------------------------------------------------------------
 
-size_t tc_smem() { return TC_SMEM; }
+// floats of one record buffer (one direction, one step parity)
+static size_t tc_records_floats(const Params& p) { return (size_t)p.N * (p.nblk + 1) * TC_REC; }
 
 void launch_tc_records(fse_ctx* c, int k, cudaStream_t st) {
     const Params& p = c->p;
@@ -434,11 +499,12 @@ void launch_tc_records(fse_ctx* c, int k, cudaStream_t st) {
     const size_t dsz = (size_t)p.N * p.nblk * FSE_BLK * FSE_BLK * 4;
     const float* Lr = reinterpret_cast<const float*>((const char*)c->d.Lr + f * fsz);
     const float* Dv = reinterpret_cast<const float*>((const char*)c->d.Dinv + f * dsz);
-    k_tc_records<<<dim3(p.nblk, p.N, 2), 256, 0, st>>>(p.n, p.b, p.nblk, p.ND, Lr, Dv, (float*)c->d.Tf,
-                                                        (float*)c->d.Tb);
+    const size_t ro = (size_t)f * tc_records_floats(p);
+    k_tc_records<<<dim3(p.nblk, p.N, 2), 256, 0, st>>>(p.n, p.b, p.nblk, p.ND, Lr, Dv, (float*)c->d.Tf + ro,
+                                                        (float*)c->d.Tb + ro);
 }
 
-void launch_tc_solve(fse_ctx* c, int phase, cudaStream_t st) {
+void launch_tc_solve(fse_ctx* c, int k, int phase, cudaStream_t st) {
     const Params& p = c->p;
     static std::atomic<unsigned long long> attr{0};
     if (needs_device_setup(attr)) {
@@ -457,11 +523,12 @@ void launch_tc_solve(fse_ctx* c, int phase, cudaStream_t st) {
     A.V = (float*)c->d.V;
     A.Y = (float*)c->d.Y;
     dim3 g((p.ld + TC_M - 1) / TC_M, p.N);
+    const size_t ro = (size_t)(k % 2) * tc_records_floats(p);
     if (phase == 1) {
-        A.rec = (const float*)c->d.Tf;
+        A.rec = (const float*)c->d.Tf + ro;
         k_tc_solve<true><<<g, TC_THREADS, TC_SMEM, st>>>(A);
     } else {
-        A.rec = (const float*)c->d.Tb;
+        A.rec = (const float*)c->d.Tb + ro;
         k_tc_solve<false><<<g, TC_THREADS, TC_SMEM, st>>>(A);
     }
 }
