@@ -467,6 +467,12 @@ static int setup_impl(const fse_model* m, const fse_opts* o, long long s_begin, 
     std::vector<int> gslot(grp.col.size()), kslot(p.kt_ld, 0);
     for (size_t q = 0; q < grp.col.size(); ++q) gslot[q] = grp.col[q] % p.RW;
     for (size_t q = 0; q < kcol.size(); ++q) kslot[q] = kcol[q] % p.RW;
+    // panel Cholesky in the state kernel for FP32 factors with b <= 96 when its window fits
+    p.chol_blk = 0;
+    if (p.prec == FSE_MIXED_FP32 && b <= 96) {
+        p.chol_blk = 1;
+        if (fse::state_smem(p) > 220 * 1024) p.chol_blk = 0;
+    }
     p.smem_state = fse::state_smem(p);
     p.smem_rhs = fse::rhs_smem(p);
     p.smem_trsm = fse::trsm_smem(p);

@@ -141,6 +141,7 @@ struct Params {
     int ND = 0;              // 32-row blocks coupled to a block through the band: ceil(b / 32)
     bool tc_ok = false;      // the tensor-core solves apply (FP32 tangents, b <= 96)
     bool has_vel = false;    // some element depends on qdot (C_t != 0)
+    int chol_blk = 0;        // the state kernel factors K_eff by 32-column panels (FP32, b <= 96)
     double tol = 0;
     size_t smem_state = 0, smem_rhs = 0, smem_trsm = 0;
 };

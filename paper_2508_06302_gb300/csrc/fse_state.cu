@@ -285,6 +285,235 @@ __device__ int cta_band_cholesky_r(T* Ac, T* Lr, T* Linv, int n, int b, T* colbu
     return bad;
 }
 
+// Panel (blocked, right-looking) banded Cholesky for FP32 factors, b <= 96, 256 threads.
+// K_eff = L L^T is factored by panels of 32 columns j0 .. j0 + 31:
+//   [L11; L21] = the panel's columns, factored column by column: L11 = chol(A11) for the
+//                32 x 32 diagonal block and L21 = A21 L11^-T for the rows j0 + 32 .. j0 + 31 + b
+//   A22 -= L21 L21^T   the trailing band
+// One thread per row of the panel (warps 0-4): rows of the diagonal block (lanes of warp 0,
+// which also form the pivots), the rows below it, and 32 rows that start as the identity and,
+// swept the same way, end as the columns of L11^-1 (the diagonal-block inverse that the tangent
+// solves use: x L11^T = e_c gives x = column c of L11^-1).  Per column one named barrier of
+// these five warps instead of one CTA barrier per column of the unblocked form; the trailing
+// update (4 x 4 register tiles, all warps) and the CTA barriers come once per panel.  Warps 5-7
+// write the previous panel's columns of L out (column band, row band, Linv, block inverse and
+// the tangent-solve records) while the panel is factored, and stage from the assembled band the
+// columns that the next panel updates first.
+// Shared workspace (floats): a ring of CHB_R columns of the band (column c in slot c mod CHB_R,
+// entry c + r at r), L21 transposed [32][CHB_RP], L11^-1 of two panels [2][32][33], 1/L_jj of
+// two panels, two buffers of the current column of L11.
+constexpr int CHB_R = 160;    // >= b + 64 columns are live at once
+constexpr int CHB_RP = 100;   // row pitch of the transposed L21 (>= b, a multiple of 4)
+__host__ __device__ constexpr size_t chol_blk_floats(int nb) {
+    return (size_t)CHB_R * nb + 32 * CHB_RP + 2 * 32 * 33 + 64 + 64;
+}
+
+// column c of the ring: W + (c mod CHB_R) nb
+__device__ __forceinline__ float* chb_col(float* W, int c, int nb) { return W + (size_t)(c % CHB_R) * nb; }
+
+// The panel factor and the trailing update are separate (not inlined) functions: inlined into the
+// panel loop, their 32-entry register arrays were kept in local memory.
+//
+// Panel at column j0 (threads 0-159): thread t < 32 row j0 + t of the diagonal block (the
+// identity past n), 32 <= t < 32 + nr row j0 + t, 128 <= t < 160 identity row t - 128; each
+// thread keeps its row in registers.  li[k] gets 1 / L_kk; L goes back into the ring, L21
+// transposed into P, L11^-1 into Zo[i * 33 + c].  Returns false (thread 0) on a non-positive or
+// non-finite pivot.  (A version with the rows in shared memory and compact loops measured 2.7x
+// slower: every row update then waits on a shared-memory round trip.)
+__device__ __noinline__ bool chb_panel(int W_o, int li_o, int cb_o, int P_o, int Zo_o, int j0, int jb, int nr, int b,
+                                       int nb) {
+    extern __shared__ float chb_dyn[];   // the kernel's dynamic shared memory: plain shared loads and stores
+    float *W = chb_dyn + W_o, *li = chb_dyn + li_o, *cb = chb_dyn + cb_o, *P = chb_dyn + P_o, *Zo = chb_dyn + Zo_o;
+    const int t = threadIdx.x;
+    const bool diag = t < 32, below = t >= 32 && t < 32 + nr, ident = t >= 128;
+    float a[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        float v = 0.f;
+        if (diag)
+            v = (k <= t && t < jb && t - k <= b) ? chb_col(W, j0 + k, nb)[t - k] : (k == t ? 1.f : 0.f);
+        else if (below)
+            v = (t - k <= b) ? chb_col(W, j0 + k, nb)[t - k] : 0.f;
+        else if (ident)
+            v = (k == t - 128) ? 1.f : 0.f;
+        a[k] = v;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        float* c = cb + (k & 1) * 32;   // column k of L11 (two buffers: a slow row may still read k - 1)
+        if (diag) {
+            const float piv = __shfl_sync(0xffffffffu, a[k], k);
+            ok = ok && (piv > 0.f) && (piv < INFINITY);
+            const float inv = rsqrtf(piv);   // 1 / L_kk (FP32 factor: refined by the FP64 residual)
+            const float l = (t == k) ? piv * inv : (t > k ? a[k] * inv : 0.f);
+            a[k] = l;
+            c[t] = l;
+            if (t == k) li[k] = inv;
+        }
+        asm volatile("bar.sync 1, 160;\n" ::: "memory");
+        if (!diag) a[k] *= li[k];
+#pragma unroll
+        for (int m = k + 1; m < 32; ++m) a[m] = fmaf(-a[k], c[m], a[m]);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (diag) {
+            if (k <= t && t < jb && t - k <= b) chb_col(W, j0 + k, nb)[t - k] = a[k];
+        } else if (below) {
+            if (t - k <= b) chb_col(W, j0 + k, nb)[t - k] = a[k];
+            P[k * CHB_RP + (t - 32)] = a[k];
+        } else if (ident) {
+            Zo[k * 33 + (t - 128)] = a[k];
+        }
+    }
+    return ok;
+}
+
+// A22 -= L21 L21^T over the nr x nr lower triangle of the trailing band: 4 x 4 tiles (ti, tc),
+// tc <= ti, tiles t = tid, tid + 256, ...
+__device__ __noinline__ void chb_update(int W_o, int P_o, int j0, int nr, int nb) {
+    extern __shared__ float chb_dyn[];
+    float* W = chb_dyn + W_o;
+    const float* P = chb_dyn + P_o;
+    const int nt4 = (nr + 3) >> 2, ntile = nt4 * (nt4 + 1) / 2;
+    for (int t = threadIdx.x; t < ntile; t += 256) {
+        int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+        while (ti * (ti + 1) / 2 > t) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        const int tc = t - ti * (ti + 1) / 2;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const float4 x = *reinterpret_cast<const float4*>(P + k * CHB_RP + 4 * ti);
+            const float4 y = *reinterpret_cast<const float4*>(P + k * CHB_RP + 4 * tc);
+            const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xv[u], yv[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int ii = 4 * ti + u, cc = 4 * tc + v;
+                if (ii < nr && cc <= ii) chb_col(W, j0 + 32 + cc, nb)[ii - cc] -= acc[u][v];
+            }
+    }
+}
+
+__device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* Dinv, int n, int b, float* ws,
+                                     float* Rf, float* Rb, int RECE) {
+    const int nb = b + 1;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float* W = ws;
+    float* P = W + (size_t)CHB_R * nb;   // P[k * CHB_RP + i'] = L(j0 + 32 + i', j0 + k)
+    float* Z = P + 32 * CHB_RP;          // panel q: Z[(q & 1) * 1056 + i * 33 + c] = (L11^-1)(i, c)
+    float* Li = Z + 2 * 32 * 33;         // 1/L_jj of panels of even / odd index
+    float* cb = Li + 64;                 // column k of L11, two buffers
+    // offsets (floats) of the workspace parts in the dynamic shared memory, for the panel bodies
+    extern __shared__ float chb_dyn[];
+    const int o_W = (int)(W - chb_dyn), o_P = (int)(P - chb_dyn), o_Z = (int)(Z - chb_dyn), o_Li = (int)(Li - chb_dyn),
+              o_cb = (int)(cb - chb_dyn);
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    // rows i < b of the row band have no columns j < 0
+    for (int idx = tid; idx < min(b, n) * b; idx += 256) {
+        const int i = idx / b, c = idx - i * b;
+        if (c < b - i) Lr[(size_t)i * nb + c] = 0.f;
+    }
+    // columns [c0, c1) of the assembled band into the ring, zero past n; threads t0 .. t0 + nthr - 1
+    auto stage = [&](int c0, int c1, int t0, int nthr) {
+        for (int c = c0; c < c1; ++c) {
+            float* d = chb_col(W, c, nb);
+            const float* g = Ac + (size_t)c * nb;
+            for (int r = tid - t0; r < nb; r += nthr) {
+                if (c + r < n)
+                    cp_async_elem(d + r, g + r);
+                else
+                    d[r] = 0.f;
+            }
+        }
+        cp_async_commit();
+    };
+    // write panel q's columns of L out of the ring; threads t0 .. t0 + nthr - 1
+    auto write_panel = [&](int q, int t0, int nthr) {
+        const int j0 = 32 * q, jb = min(32, n - j0), t = tid - t0;
+        const float* li = Li + (q & 1) * 32;
+        const float* Zq = Z + (q & 1) * 32 * 33;
+        for (int k = 0; k < jb; ++k) {   // column band, contiguous
+            const float* src = chb_col(W, j0 + k, nb);
+            float* dst = Ac + (size_t)(j0 + k) * nb;
+            for (int r = t; r < nb; r += nthr) dst[r] = (j0 + k + r < n) ? src[r] : 0.f;
+        }
+        const int rows = min(n, j0 + 32 + b) - j0;
+        for (int idx = t; idx < rows * 32; idx += nthr) {   // row band and backward records, j fastest
+            const int ip = idx >> 5, k = idx & 31, i = j0 + ip, j = j0 + k, r = ip - k;
+            if (k >= jb || r < 0 || r > b) continue;
+            const float v = chb_col(W, j, nb)[r];
+            Lr[(size_t)i * nb + (b - r)] = v;
+            if (Rb && ip >= 32) Rb[(size_t)q * RECE + (ip - 32) * FSE_BLK + k] = v;
+        }
+        if (Rf) {
+            const int rb = rows - 32;   // rows below the diagonal block
+            for (int k = 0; k < jb; ++k) {   // forward records, i fastest
+                const int j = j0 + k;
+                const float* src = chb_col(W, j, nb);
+                for (int ii = t; ii < rb; ii += nthr) {
+                    const int i = j0 + 32 + ii, r = i - j, i0 = i & ~(FSE_BLK - 1);
+                    if (r <= b) Rf[(size_t)(i >> 5) * RECE + (j - i0 + b) * FSE_BLK + (i - i0)] = src[r];
+                }
+            }
+        }
+        for (int k = t; k < jb; k += nthr) Linv[j0 + k] = li[k];
+        float* D = Dinv + (size_t)q * FSE_BLK * FSE_BLK;
+        const int dofs = RECE - FSE_BLK * FSE_BLK;
+        for (int idx = t; idx < FSE_BLK * FSE_BLK; idx += nthr) {
+            const int i = idx >> 5, c = idx & 31;
+            const float z = Zq[i * 33 + c];
+            D[idx] = z;
+            if (Rf && Rb) {
+                Rb[(size_t)q * RECE + dofs + idx] = z;                 // backward record: Dinv
+                Rf[(size_t)q * RECE + dofs + c * FSE_BLK + i] = z;     // forward record: Dinv^T
+            }
+        }
+    };
+    stage(0, min(n, 32 + b), 0, 256);
+    cp_async_wait0();
+    __syncthreads();
+    const int npan = (n + FSE_BLK - 1) / FSE_BLK;
+    int p = 0;
+    for (; p < npan; ++p) {
+        const int j0 = 32 * p, jb = min(32, n - j0);
+        const int nr = max(0, min(n, j0 + 32 + b) - (j0 + 32));   // rows of L21 (<= b)
+        if (tid < 160) {
+            const bool ok = chb_panel(o_W, o_Li + (p & 1) * 32, o_cb, o_P, o_Z + (p & 1) * 32 * 33, j0, jb, nr, b, nb);
+            if (tid == 0 && !ok) bad = 1;
+        } else if (p > 0) {
+            write_panel(p - 1, 160, 96);
+        }
+        __syncthreads();
+        if (bad) break;
+        // columns first updated by panel p + 1; their ring slots held panels < p, written out above
+        if (warp >= 4) {
+            const int c0 = 32 * (p + 1) + b;
+            stage(min(n, c0), min(n, c0 + 32), 128, 128);
+        }
+        chb_update(o_W, o_P, j0, nr, nb);
+        cp_async_wait0();
+        __syncthreads();
+    }
+    if (p == npan) write_panel(npan - 1, 0, 256);
+    cp_async_wait0();
+    __syncthreads();
+    return bad;
+}
+
 // FP32 factors with b + 1 <= 96 keep the window in registers; others use the shared window
 template <typename T>
 __device__ int band_cholesky(T* Ac, T* Lr, T* Linv, int n, int b, T* wnd, T* stg, T* Rf, T* Rb, int RECE) {
@@ -342,6 +571,14 @@ __device__ void cta_diag_inverses(const T* Lr, const T* Linv, int n, int b, int 
 }
 
 
+// span (elements of the factor precision) of the state kernel's factorisation workspace
+__host__ __device__ inline size_t state_wspan(int nb, int blk) {
+    const size_t a = (size_t)(nb + 1 + FSE_CHOL_PF) * nb, d = (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK);
+    size_t w = a > d ? a : d;
+    if (blk && chol_blk_floats(nb) > w) w = chol_blk_floats(nb);
+    return w;
+}
+
 // ----------------------------------------------------------------------------
 // the state kernel
 // ----------------------------------------------------------------------------
@@ -370,8 +607,21 @@ struct StateArgs {
     void *oLc, *oLr, *oLinv, *oDinv;         // factor of K_eff at the new state
     void *oRf, *oRb;                         // its block records for the tangent solves
     int RECE;
+    int chol_blk;       // factor K_eff by 32-column panels (FP32, b <= 96)
     int *status, *iters, *nref;
 };
+
+// factor of K_eff (column band Ac in place, row band, 1/L_jj, diagonal-block inverses and the
+// tangent-solve records); nonzero on a non-positive or non-finite pivot
+template <typename T, bool BLK>
+__device__ int band_factor(const StateArgs& A, T* Ac, T* Lr, T* Linv, T* Dinv, T* wnd, T* stg, T* Rf, T* Rb) {
+    if constexpr (BLK) {
+        return cta_band_cholesky_blk(Ac, Lr, Linv, Dinv, A.n, A.b, wnd, Rf, Rb, A.RECE);
+    }
+    const int bad = band_cholesky<T>(Ac, Lr, Linv, A.n, A.b, wnd, stg, Rf, Rb, A.RECE);
+    if (!bad) cta_diag_inverses<T>(Lr, Linv, A.n, A.b, A.nblk, Dinv, wnd, Rf, Rb, A.RECE);
+    return bad;
+}
 
 __device__ __forceinline__ double forcing_i(const StateArgs& A, int s, int i, double phi) {
     double e = A.F[i] * cos(phi);
@@ -604,8 +854,10 @@ __device__ void warp_band_solve_fp64(const double* __restrict__ Lc, const double
     }
 }
 
-template <typename T>
+// BLK: FP32 factor by 32-column panels (the launcher picks it when chol_blk is set)
+template <typename T, bool BLK>
 __global__ void __launch_bounds__(256) k_state(StateArgs A) {
+    static_assert(!BLK || sizeof(T) == 4, "panel Cholesky is FP32 only");
     const int s = blockIdx.x, n = A.n, b = A.b, nb = b + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     extern __shared__ double sm[];
@@ -615,7 +867,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     // tiles of cta_diag_inverses reuse the same space once the factorisation is done
     T* wnd = reinterpret_cast<T*>(sr + n + FSE_BLK);
     T* stg = wnd + (size_t)(nb + 1) * nb;
-    const size_t wspan = max((size_t)(nb + 1 + FSE_CHOL_PF) * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
+    const size_t wspan = state_wspan(nb, BLK ? 1 : 0);
     T* ysol = wnd + wspan;                                // n: solve vector in the factor precision
     // physical velocities qdot = w u of the current iterate (velocity-dependent elements only)
     double* sv = A.has_vel
@@ -729,12 +981,11 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
                 ++nref;
                 vel_iterate();
                 assemble_keff<T>(A, s, sqn, sv, oLc, kt_out, ct_out);
-                if (band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE)) {
+                if (band_factor<T, BLK>(A, oLc, oLr, oLi, oDi, wnd, stg, oRf, oRb)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
                     break;
                 }
-                cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
                 __syncthreads();
                 cLc = oLc;
                 cLr = oLr;
@@ -787,8 +1038,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
                 rom[i] = T((double)rom[i] - acc);
             }
         }
-        bad = band_cholesky<T>(oLc, oLr, oLi, n, b, wnd, stg, oRf, oRb, A.RECE);
-        if (!bad) cta_diag_inverses<T>(oLr, oLi, n, b, A.nblk, oDi, wnd, oRf, oRb, A.RECE);
+        bad = band_factor<T, BLK>(A, oLc, oLr, oLi, oDi, wnd, stg, oRf, oRb);
     }
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
@@ -858,7 +1108,7 @@ int launch_factor_M(fse_ctx* c) {
 size_t state_smem(const Params& p) {
     const int nb = p.b + 1;
     const size_t tsz = p.prec == FSE_MIXED_FP32 ? 4 : 8;
-    const size_t wspan = std::max((size_t)(nb + 1 + FSE_CHOL_PF) * nb, (size_t)8 * (FSE_BLK * FSE_BLK + FSE_BLK));
+    const size_t wspan = state_wspan(nb, tsz == 4 ? p.chol_blk : 0);
     return (size_t)(6 * p.n + FSE_BLK) * 8 + (wspan + (size_t)p.n) * tsz + (p.has_vel ? (size_t)p.n * 8 + 8 : 0);
 }
 
@@ -935,20 +1185,31 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.oRf = (char*)c->d.Rf + fo * rsz;
     A.oRb = (char*)c->d.Rb + fo * rsz;
     A.RECE = p.RECE;
+    A.chol_blk = p.chol_blk;
     A.status = c->d.status;
     A.iters = c->d.iters;
     A.nref = c->d.nref;
     return A;
 }
 
-template <typename T>
-static void state_launch(fse_ctx* c, const StateArgs& A, cudaStream_t st) {
+template <typename T, bool BLK>
+static void state_launch_k(fse_ctx* c, const StateArgs& A, cudaStream_t st) {
     static std::atomic<unsigned long long> attr_set{0};
     if (needs_device_setup(attr_set)) {
-        cudaFuncSetAttribute(k_state<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(k_state<T, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         mark_device(attr_set);
     }
-    k_state<T><<<c->p.N, 256, c->p.smem_state, st>>>(A);
+    k_state<T, BLK><<<c->p.N, 256, c->p.smem_state, st>>>(A);
+}
+template <typename T>
+static void state_launch(fse_ctx* c, const StateArgs& A, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (A.chol_blk) {
+            state_launch_k<float, true>(c, A, st);
+            return;
+        }
+    }
+    state_launch_k<T, false>(c, A, st);
 }
 
 __global__ void k_split(int N, int n, const double* zb, double* q, double* u) {
