@@ -290,22 +290,22 @@ __device__ int cta_band_cholesky_r(T* Ac, T* Lr, T* Linv, int n, int b, T* colbu
 //   [L11; L21] = the panel's columns, factored column by column: L11 = chol(A11) for the
 //                32 x 32 diagonal block and L21 = A21 L11^-T for the rows j0 + 32 .. j0 + 31 + b
 //   A22 -= L21 L21^T   the trailing band
-// One thread per row of the panel (warps 0-4): rows of the diagonal block (lanes of warp 0,
-// which also form the pivots), the rows below it, and 32 rows that start as the identity and,
-// swept the same way, end as the columns of L11^-1 (the diagonal-block inverse that the tangent
-// solves use: x L11^T = e_c gives x = column c of L11^-1).  Per column one named barrier of
-// these five warps instead of one CTA barrier per column of the unblocked form; the trailing
-// update (4 x 4 register tiles, all warps) and the CTA barriers come once per panel.  Warps 5-7
-// write the previous panel's columns of L out (column band, row band, Linv, block inverse and
-// the tangent-solve records) while the panel is factored, and stage from the assembled band the
+// The panel is factored by warps 0-4 without a barrier: each factors its own copy of the
+// diagonal block through shuffles and sweeps one row of its own with the same column operations
+// (the rows below the block; for warp 4, rows that start as the identity and end as the columns
+// of L11^-1, the diagonal-block inverse the tangent solves use: x L11^T = e_c gives x = column c
+// of L11^-1).  The trailing update (4 x 4 register tiles, all warps) and two CTA barriers come
+// once per panel, against one barrier per column in the unblocked form.  Warps 5-7 write the
+// previous panel's columns of L out (column band, row band, Linv, block inverse and the tangent-
+// solve records) while the panel is factored; warps 4-7 then stage from the assembled band the
 // columns that the next panel updates first.
 // Shared workspace (floats): a ring of CHB_R columns of the band (column c in slot c mod CHB_R,
 // entry c + r at r), L21 transposed [32][CHB_RP], L11^-1 of two panels [2][32][33], 1/L_jj of
-// two panels, two buffers of the current column of L11.
+// two panels.
 constexpr int CHB_R = 160;    // >= b + 64 columns are live at once
 constexpr int CHB_RP = 100;   // row pitch of the transposed L21 (>= b, a multiple of 4)
 __host__ __device__ constexpr size_t chol_blk_floats(int nb) {
-    return (size_t)CHB_R * nb + 32 * CHB_RP + 2 * 32 * 33 + 64 + 64;
+    return (size_t)CHB_R * nb + 32 * CHB_RP + 2 * 32 * 33 + 64;
 }
 
 // column c of the ring: W + (c mod CHB_R) nb
@@ -314,57 +314,52 @@ __device__ __forceinline__ float* chb_col(float* W, int c, int nb) { return W + 
 // The panel factor and the trailing update are separate (not inlined) functions: inlined into the
 // panel loop, their 32-entry register arrays were kept in local memory.
 //
-// Panel at column j0 (threads 0-159): thread t < 32 row j0 + t of the diagonal block (the
-// identity past n), 32 <= t < 32 + nr row j0 + t, 128 <= t < 160 identity row t - 128; each
-// thread keeps its row in registers.  li[k] gets 1 / L_kk; L goes back into the ring, L21
-// transposed into P, L11^-1 into Zo[i * 33 + c].  Returns false (thread 0) on a non-positive or
-// non-finite pivot.  (A version with the rows in shared memory and compact loops measured 2.7x
-// slower: every row update then waits on a shared-memory round trip.)
-__device__ __noinline__ bool chb_panel(int W_o, int li_o, int cb_o, int P_o, int Zo_o, int j0, int jb, int nr, int b,
-                                       int nb) {
+// Panel at column j0 (threads 0-159, five warps, no barrier): every warp factors its own copy of
+// the diagonal block (lane i: row j0 + i, the identity past n) with shuffles, and applies the
+// same column operations to one row of its own: warps 1-3 the rows j0 + 32 .. j0 + 127 below the
+// block (rows past j0 + 31 + nr are zero), warp 4 the identity rows that become the columns of
+// L11^-1.  li[k] gets 1 / L_kk; L goes back into the ring, L21 transposed into P, L11^-1 into
+// Zo[i * 33 + c].  Returns false (warp 0) on a non-positive or non-finite pivot.  (Forming the
+// pivots once and sharing each column through shared memory and a barrier per column measured
+// 3-4x slower: the barrier chain set the pace.)
+__device__ __noinline__ bool chb_panel(int W_o, int li_o, int P_o, int Zo_o, int j0, int jb, int nr, int b, int nb) {
     extern __shared__ float chb_dyn[];   // the kernel's dynamic shared memory: plain shared loads and stores
-    float *W = chb_dyn + W_o, *li = chb_dyn + li_o, *cb = chb_dyn + cb_o, *P = chb_dyn + P_o, *Zo = chb_dyn + Zo_o;
-    const int t = threadIdx.x;
-    const bool diag = t < 32, below = t >= 32 && t < 32 + nr, ident = t >= 128;
-    float a[32];
+    float *W = chb_dyn + W_o, *li = chb_dyn + li_o, *P = chb_dyn + P_o, *Zo = chb_dyn + Zo_o;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int ib = 32 * (w - 1) + lane;   // warps 1-3: row j0 + 32 + ib
+    const bool below = w >= 1 && w <= 3 && ib < nr, ident = w == 4;
+    float d[32], a[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        float v = 0.f;
-        if (diag)
-            v = (k <= t && t < jb && t - k <= b) ? chb_col(W, j0 + k, nb)[t - k] : (k == t ? 1.f : 0.f);
-        else if (below)
-            v = (t - k <= b) ? chb_col(W, j0 + k, nb)[t - k] : 0.f;
-        else if (ident)
-            v = (k == t - 128) ? 1.f : 0.f;
-        a[k] = v;
+        d[k] = (k <= lane && lane < jb && lane - k <= b) ? chb_col(W, j0 + k, nb)[lane - k] : (k == lane ? 1.f : 0.f);
+        a[k] = below ? ((32 + ib - k <= b) ? chb_col(W, j0 + k, nb)[32 + ib - k] : 0.f) : ((ident && k == lane) ? 1.f : 0.f);
     }
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        float* c = cb + (k & 1) * 32;   // column k of L11 (two buffers: a slow row may still read k - 1)
-        if (diag) {
-            const float piv = __shfl_sync(0xffffffffu, a[k], k);
-            ok = ok && (piv > 0.f) && (piv < INFINITY);
-            const float inv = rsqrtf(piv);   // 1 / L_kk (FP32 factor: refined by the FP64 residual)
-            const float l = (t == k) ? piv * inv : (t > k ? a[k] * inv : 0.f);
-            a[k] = l;
-            c[t] = l;
-            if (t == k) li[k] = inv;
-        }
-        asm volatile("bar.sync 1, 160;\n" ::: "memory");
-        if (!diag) a[k] *= li[k];
+        const float piv = __shfl_sync(0xffffffffu, d[k], k);
+        ok = ok && (piv > 0.f) && (piv < INFINITY);
+        const float inv = rsqrtf(piv);   // 1 / L_kk (FP32 factor: refined by the FP64 residual)
+        const float lk = (lane == k) ? piv * inv : (lane > k ? d[k] * inv : 0.f);
+        d[k] = lk;
+        a[k] *= inv;
+        if (w == 0 && lane == k) li[k] = inv;
 #pragma unroll
-        for (int m = k + 1; m < 32; ++m) a[m] = fmaf(-a[k], c[m], a[m]);
+        for (int m = k + 1; m < 32; ++m) {
+            const float lm = __shfl_sync(0xffffffffu, lk, m);   // L(j0 + m, j0 + k)
+            d[m] = fmaf(-lk, lm, d[m]);
+            a[m] = fmaf(-a[k], lm, a[m]);
+        }
     }
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        if (diag) {
-            if (k <= t && t < jb && t - k <= b) chb_col(W, j0 + k, nb)[t - k] = a[k];
+        if (w == 0) {
+            if (k <= lane && lane < jb && lane - k <= b) chb_col(W, j0 + k, nb)[lane - k] = d[k];
         } else if (below) {
-            if (t - k <= b) chb_col(W, j0 + k, nb)[t - k] = a[k];
-            P[k * CHB_RP + (t - 32)] = a[k];
+            if (32 + ib - k <= b) chb_col(W, j0 + k, nb)[32 + ib - k] = a[k];
+            P[k * CHB_RP + ib] = a[k];
         } else if (ident) {
-            Zo[k * 33 + (t - 128)] = a[k];
+            Zo[k * 33 + lane] = a[k];
         }
     }
     return ok;
@@ -415,11 +410,9 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
     float* P = W + (size_t)CHB_R * nb;   // P[k * CHB_RP + i'] = L(j0 + 32 + i', j0 + k)
     float* Z = P + 32 * CHB_RP;          // panel q: Z[(q & 1) * 1056 + i * 33 + c] = (L11^-1)(i, c)
     float* Li = Z + 2 * 32 * 33;         // 1/L_jj of panels of even / odd index
-    float* cb = Li + 64;                 // column k of L11, two buffers
     // offsets (floats) of the workspace parts in the dynamic shared memory, for the panel bodies
     extern __shared__ float chb_dyn[];
-    const int o_W = (int)(W - chb_dyn), o_P = (int)(P - chb_dyn), o_Z = (int)(Z - chb_dyn), o_Li = (int)(Li - chb_dyn),
-              o_cb = (int)(cb - chb_dyn);
+    const int o_W = (int)(W - chb_dyn), o_P = (int)(P - chb_dyn), o_Z = (int)(Z - chb_dyn), o_Li = (int)(Li - chb_dyn);
     __shared__ int bad;
     if (tid == 0) bad = 0;
     // rows i < b of the row band have no columns j < 0
@@ -492,7 +485,7 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
         const int j0 = 32 * p, jb = min(32, n - j0);
         const int nr = max(0, min(n, j0 + 32 + b) - (j0 + 32));   // rows of L21 (<= b)
         if (tid < 160) {
-            const bool ok = chb_panel(o_W, o_Li + (p & 1) * 32, o_cb, o_P, o_Z + (p & 1) * 32 * 33, j0, jb, nr, b, nb);
+            const bool ok = chb_panel(o_W, o_Li + (p & 1) * 32, o_P, o_Z + (p & 1) * 32 * 33, j0, jb, nr, b, nb);
             if (tid == 0 && !ok) bad = 1;
         } else if (p > 0) {
             write_panel(p - 1, 160, 96);
