@@ -476,7 +476,19 @@ typedef struct {
     double ms;                 /* device time of the point                      */
     int status;                /* FSE_OK when accepted                          */
     int predictor;             /* predictor actually used                       */
+    int fallback;              /* 1: accepted by the FP64 fallback context       */
 } fse_cont_point;
+
+/* Attach (fb non-NULL) or detach (fb NULL) an FP64 context of the same problem to an
+ * FSE_MIXED_FP32 context.  A point that the mixed-precision corrector of fse_continue does not
+ * accept (no contraction within max_newton updates, or a non-finite trajectory: FP32 tangents
+ * can be too coarse for a nearly undamped structure, whose Floquet multipliers sit close to
+ * the unit circle) is corrected again from the same prediction in fb with the same options,
+ * and its torus is copied back; fse_cont_point.fallback records it.  The paper has no
+ * counterpart (it uses one precision).  Both contexts must be unsharded, on the same device,
+ * with equal n, d, S, H, rho and S1 (checked: n, d, U~, N, S1 and rho); the caller keeps fb
+ * alive while attached and sets its linear solver.  Returns FSE_EINVAL on a mismatch. */
+int fse_set_fallback(fse_ctx* ctx, fse_ctx* fb);
 
 /* Run the sweep.  Z_start: host, 2 n U~ doubles (initial guess of point 0);
  * Z_out: host, n_points x 2 n U~ (nullable); info: n_points records (nullable).

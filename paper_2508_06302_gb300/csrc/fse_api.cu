@@ -1659,6 +1659,7 @@ extern "C" int fse_continue_arclength(fse_ctx* c, const fse_arc_opts* o, const d
             info[j].ms = ms;
             info[j].status = pst;
             info[j].predictor = FSE_PRED_SECANT;
+            info[j].fallback = 0;
         }
         if (n_done) *n_done = j + 1;
     };
@@ -1825,6 +1826,22 @@ extern "C" int fse_timings(fse_ctx* c, double* ms, int cap) {
 // one-parameter continuation in w_1 with the secant or the learned predictor
 // ----------------------------------------------------------------------------
 
+extern "C" int fse_set_fallback(fse_ctx* c, fse_ctx* fb) {
+    if (!c) return FSE_EINVAL;
+    if (!fb) {
+        c->fallback = nullptr;
+        return FSE_OK;
+    }
+    if (fb == c || c->p.prec != FSE_MIXED_FP32 || fb->p.prec != FSE_FP64)
+        return set_err(c, FSE_EINVAL, "fallback: an FP64 context for an FSE_MIXED_FP32 one");
+    if (c->p.shard || fb->p.shard) return set_err(c, FSE_EINVAL, "fallback: trajectory shards are not supported");
+    if (fb->device != c->device || fb->p.n != c->p.n || fb->p.d != c->p.d || fb->p.U != c->p.U ||
+        fb->p.N != c->p.N || fb->p.S1 != c->p.S1 || fb->rho != c->rho)
+        return set_err(c, FSE_EINVAL, "fallback: a context of another problem (n, d, U, N, S1, rho or device)");
+    c->fallback = fb;
+    return FSE_OK;
+}
+
 extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, const double* Z_start,
                             double* Z_out, fse_cont_point* info) {
     if (!c || !o || !Z_start || !o->omega1 || o->n_points < 1) return FSE_EINVAL;
@@ -1940,7 +1957,56 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
             st = eval_at_iterate(c, w, 1, &rn, &zn);
             ++evals;
         }
-        const int pst = (st < 0) ? st : (rn <= o->rel_tol * zn ? FSE_OK : FSE_ENOCONV);
+        int pst = (st < 0) ? st : (rn <= o->rel_tol * zn ? FSE_OK : FSE_ENOCONV);
+        // a point the mixed-precision corrector rejects is corrected again in the FP64 context
+        bool fell_back = false;
+        if (pst != FSE_OK && pst != FSE_ECUDA && c->fallback) {
+            fse_ctx* fb = c->fallback;
+            if (fb->rho != c->rho) {
+                cleanup();
+                return set_err(c, FSE_EINVAL, "fallback context has other rotation numbers");
+            }
+            int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "continuation point");
+            if (!rc) rc = cuda_check(c, cudaMemcpy(fb->d.Z0, Zp, nu * 8, cudaMemcpyDeviceToDevice), "fallback start");
+            if (rc) {
+                cleanup();
+                return rc;
+            }
+            int fst = eval_at_iterate(fb, w, 1, &rn, &zn);
+            ++evals;
+            int fit = 0;
+            while (fst >= FSE_ENOCONV && rn > o->rel_tol * zn && fit < o->max_newton) {
+                const int frc = newton_solve_update(fb);
+                if (frc && frc != FSE_ENOCONV) {
+                    fst = frc;
+                    break;
+                }
+                ++fit;
+                fst = eval_at_iterate(fb, w, 0, &rn, &zn);
+                ++evals;
+                if (rn <= o->rel_tol * zn || fst < FSE_ENOCONV) break;
+                if (o->chord) continue;
+                fst = eval_at_iterate(fb, w, 1, &rn, &zn);
+                ++evals;
+            }
+            it += fit;
+            pst = (fst < 0) ? fst : (rn <= o->rel_tol * zn ? FSE_OK : FSE_ENOCONV);
+            if (fst == FSE_ECUDA) {
+                c->err = "fallback context: " + fb->err;
+                cleanup();
+                return FSE_ECUDA;
+            }
+            rc = cuda_check(c, cudaStreamSynchronize(fb->stream), "fallback point");
+            if (!rc) rc = cuda_check(c, cudaMemcpy(c->d.Z0, fb->d.Z0, nu * 8, cudaMemcpyDeviceToDevice), "fallback torus");
+            if (rc) {
+                cleanup();
+                return rc;
+            }
+            // the mixed context's monodromies belong to the rejected iterate: the next point's
+            // first evaluation recomputes them
+            c->have_jac = false;
+            fell_back = true;
+        }
         if (pst != FSE_OK && (worst == FSE_OK || pst < worst)) worst = pst;
         cudaMemcpyAsync(Zs + (size_t)j * nu, c->d.Z0, nu * 8, cudaMemcpyDeviceToDevice, c->stream);
         if (Z_out) cudaMemcpyAsync(Z_out + (size_t)j * nu, c->d.Z0, nu * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -1966,6 +2032,7 @@ extern "C" int fse_continue(fse_ctx* c, fse_mlp* mlp, const fse_cont_opts* o, co
             info[j].ms = ms;
             info[j].status = pst;
             info[j].predictor = used_mlp ? FSE_PRED_MLP : FSE_PRED_SECANT;
+            info[j].fallback = fell_back ? 1 : 0;
         }
         // ---- learning: the secant's correction Z_j - S_j of every accepted point j >= 2, its
         // POD, and the network trained on the scaled coefficients

@@ -158,6 +158,7 @@ struct fse_ctx {
     cudaStream_t stream2 = nullptr;  // sensitivity kernels (overlap with the next state step)
     std::string err;
     std::vector<int> ktab_host;
+    fse_ctx* fallback = nullptr;   // FP64 context of the same problem for points the mixed form rejects
     std::vector<double> rho;
     double omega_S = -1.0;       // w_1 the operators were built for
     bool have_jac = false;

@@ -100,6 +100,7 @@ def load(path: Optional[str] = None):
         "fse_set_linear_solver": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
         "fse_linear_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "fse_set_tangent_solve": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fse_set_fallback": (ctypes.c_int, [_VP, _VP]),
         "fse_residual_jacobian_hypertime": (ctypes.c_int, [_VP, _DP, ctypes.c_double, _DP, ctypes.c_int, _IP,
                                                            _IP]),
         "fse_jacobian_apply_hypertime": (ctypes.c_int, [_VP, _DP, _DP, ctypes.c_int]),
@@ -408,6 +409,13 @@ class Context:
         k = {"auto": FSE_SOLVE_AUTO, "simt": FSE_SOLVE_SIMT, "tc": FSE_SOLVE_TC}[kind]
         self._check(load().fse_set_tangent_solve(self.h, k))
 
+    def set_fallback(self, other):
+        """fse_set_fallback: attach an FP64 Context of the same problem (None detaches); the
+        continuation driver re-corrects the points this mixed-precision context rejects there.
+        The caller keeps `other` alive while it is attached."""
+        self._fallback = other
+        self._check(load().fse_set_fallback(self.h, other.h if other is not None else None))
+
     def linear_stats(self):
         """fse_linear_stats: (Krylov iterations, relative residual) of the last outer solve."""
         it = ctypes.c_int()
@@ -591,7 +599,7 @@ class fse_cont_opts(ctypes.Structure):
 class fse_cont_point(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("evals", ctypes.c_int), ("res", ctypes.c_double),
                 ("znorm", ctypes.c_double), ("pred_err", ctypes.c_double), ("ms", ctypes.c_double),
-                ("status", ctypes.c_int), ("predictor", ctypes.c_int)]
+                ("status", ctypes.c_int), ("predictor", ctypes.c_int), ("fallback", ctypes.c_int)]
 
 
 class fse_arc_opts(ctypes.Structure):
