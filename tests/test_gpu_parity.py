@@ -252,6 +252,24 @@ def test_non_finite_start_reports_enan(precision):
     ctx.close()
 
 
+def test_lyapunov_rejects_out_of_range_sizes_before_any_launch():
+    """fse_lyapunov bounds its scratch (2n x h with 1 <= h <= min(64, 2n), N_Ly >= 1) at the
+    boundary: out-of-range sizes return FSE_EINVAL before any allocation or launch, and the
+    context then computes the exponents unchanged."""
+    fse = _fse()
+    m = I.chain(4)
+    ctx = fse.Context(m, 2, [7], [3], [0.5], 16, newton_tol=0, newton_maxit=4)
+    w1 = 1.1 * m.omega_n1
+    Z = I.random_coeffs(m.n, ctx.U, 1e-3, seed=4)
+    s0 = ctx.lyapunov(Z, w1, 20, 4)
+    for N_Ly, h in ((20, 2 * m.n + 1), (20, 65), (0, 4)):
+        with pytest.raises(fse.FSEError) as ei:
+            ctx.lyapunov(Z, w1, N_Ly, h)
+        assert ei.value.code == fse.FSE_EINVAL
+    assert np.array_equal(ctx.lyapunov(Z, w1, 20, 4), s0)
+    ctx.close()
+
+
 def test_setup_rejects_bad_input():
     fse = _fse()
     m = I.chain(4)
