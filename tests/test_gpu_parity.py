@@ -35,6 +35,9 @@ CASES = {
     "chain4_N1_H0": (lambda: I.chain(4, F=(2.0, 0.0), c=3.0), 2, [1], [0], 24, [I.GOLDEN], 1.2, 1e-3),
     # one dof (half-bandwidth 0): every tile of the solves is ragged
     "chain1_n1": (lambda: I.chain(1), 2, [5], [2], 24, [I.GOLDEN], 1.1, 1e-3),
+    # half-bandwidth 92, near the 96 limit of the panel factor and the blocked solves: the panel
+    # factor's column ring (b + 64 of its 160 columns live) and ND = 3 coupled blocks
+    "shell_b92_d2": (lambda: I.flat_shell(nx=3, ny=15), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
     # half-bandwidth 110 > 96: the tangent solves take the wide-band kernel (k_trsm)
     "shell204_wide_d2": (lambda: I.flat_shell(nx=3, ny=18), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
     "chain5_d3": (lambda: I.chain(5, F=(1.0, 0.5, 0.3)), 3, [3, 5], [1, 2], 16,
@@ -59,8 +62,9 @@ def _setup(name, precision="fp64", maxit=16):
     return m, prob, ctx, Z, w1
 
 
-# FP64 tangents with b > 96 do not fit the solves' shared-memory ring (tested below)
-FP64_CASES = [c for c in CASES if c != "shell204_wide_d2"]
+# FP64 tangents with b > 96 do not fit the solves' shared-memory ring (tested below), nor, with
+# b = 92, the FP64 solves' working set: setup rejects them (FP32 tangents only)
+FP64_CASES = [c for c in CASES if c not in ("shell204_wide_d2", "shell_b92_d2")]
 
 
 @pytest.mark.parametrize("name", FP64_CASES)
@@ -103,8 +107,8 @@ def test_jacobian_products_fp64(name):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "shell204_wide_d2", "chain5_d3",
-                                  "chain4_N1_H0", "chain1_n1"])
+@pytest.mark.parametrize("name", ["beam18_d2", "vk87_d2", "shell90_d2", "shell_b92_d2", "shell204_wide_d2",
+                                  "chain5_d3", "chain4_N1_H0", "chain1_n1"])
 def test_mixed_fp32(name):
     m, prob, ctx, Z, w1 = _setup(name, precision="mixed_fp32", maxit=16)
     ref = O.residual_jacobian(prob, Z, w1, want_jacobian=True, dense=False, tol=0, maxit=16)

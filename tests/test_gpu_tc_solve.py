@@ -26,6 +26,7 @@ CASES = {
     "shell90_d2": (lambda: I.flat_shell(nx=6, ny=4), 2, [5], [2], 20, [I.GOLDEN], 1.0, 1e-4),
     "shell150_d2": (lambda: I.flat_shell(nx=6, ny=6), 2, [3], [1], 16, [I.GOLDEN], 1.0, 1e-4),
     "shell198_d2": (lambda: I.flat_shell(nx=4, ny=12), 2, [3], [1], 16, [I.GOLDEN], 1.0, 1e-4),
+    "shell252_b92_d2": (lambda: I.flat_shell(nx=4, ny=15), 2, [3], [1], 16, [I.GOLDEN], 1.0, 1e-4),
     "chain4_N1_H0": (lambda: I.chain(4, F=(2.0, 0.0), c=3.0), 2, [1], [0], 24, [I.GOLDEN], 1.2, 1e-3),
     "plate27_d3": (lambda: I.kirchhoff_plate(nx=4, ny=4, n_springs=3), 3, [3, 3], [1, 1], 16,
                    [math.sqrt(2), math.sqrt(3)], 1.1, 1e-4),
