@@ -301,11 +301,11 @@ __device__ int cta_band_cholesky_r(T* Ac, T* Lr, T* Linv, int n, int b, T* colbu
 // columns that the next panel updates first.
 // Shared workspace (floats): a ring of CHB_R columns of the band (column c in slot c mod CHB_R,
 // entry c + r at r), L21 transposed [32][CHB_RP], L11^-1 of two panels [2][32][33], 1/L_jj of
-// two panels.
+// two panels, per panel warp two buffers of the current column of L11.
 constexpr int CHB_R = 160;    // >= b + 64 columns are live at once
 constexpr int CHB_RP = 100;   // row pitch of the transposed L21 (>= b, a multiple of 4)
 __host__ __device__ constexpr size_t chol_blk_floats(int nb) {
-    return (size_t)CHB_R * nb + 32 * CHB_RP + 2 * 32 * 33 + 64;
+    return (size_t)CHB_R * nb + 32 * CHB_RP + 2 * 32 * 33 + 64 + 5 * 64;
 }
 
 // column c of the ring: W + (c mod CHB_R) nb
@@ -322,10 +322,12 @@ __device__ __forceinline__ float* chb_col(float* W, int c, int nb) { return W + 
 // Zo[i * 33 + c].  Returns false (warp 0) on a non-positive or non-finite pivot.  (Forming the
 // pivots once and sharing each column through shared memory and a barrier per column measured
 // 3-4x slower: the barrier chain set the pace.)
-__device__ __noinline__ bool chb_panel(int W_o, int li_o, int P_o, int Zo_o, int j0, int jb, int nr, int b, int nb) {
+__device__ __noinline__ bool chb_panel(int W_o, int li_o, int P_o, int Zo_o, int cb_o, int j0, int jb, int nr, int b,
+                                       int nb) {
     extern __shared__ float chb_dyn[];   // the kernel's dynamic shared memory: plain shared loads and stores
     float *W = chb_dyn + W_o, *li = chb_dyn + li_o, *P = chb_dyn + P_o, *Zo = chb_dyn + Zo_o;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    float* cbw = chb_dyn + cb_o + w * 64;   // this warp's two buffers for the current column of L11
     const int ib = 32 * (w - 1) + lane;   // warps 1-3: row j0 + 32 + ib
     const bool below = w >= 1 && w <= 3 && ib < nr, ident = w == 4;
     float d[32], a[32];
@@ -344,11 +346,25 @@ __device__ __noinline__ bool chb_panel(int W_o, int li_o, int P_o, int Zo_o, int
         d[k] = lk;
         a[k] *= inv;
         if (w == 0 && lane == k) li[k] = inv;
+        // column k goes through the warp's buffer (k & 1) and comes back as broadcast 16-byte
+        // loads: a quarter of the shared-memory operations of one shuffle per entry.  The
+        // buffer written at step k + 1 was last read at step k - 1, before this __syncwarp.
+        float* cbk = cbw + (k & 1) * 32;
+        cbk[lane] = lk;
+        __syncwarp();
+        const float4* c4 = reinterpret_cast<const float4*>(cbk);
 #pragma unroll
-        for (int m = k + 1; m < 32; ++m) {
-            const float lm = __shfl_sync(0xffffffffu, lk, m);   // L(j0 + m, j0 + k)
-            d[m] = fmaf(-lk, lm, d[m]);
-            a[m] = fmaf(-a[k], lm, a[m]);
+        for (int g = (k + 1) / 4; g < 8; ++g) {
+            const float4 v = c4[g];   // L(j0 + 4g .. j0 + 4g + 3, j0 + k)
+            const float lv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int m = 4 * g + u;
+                if (m > k) {
+                    d[m] = fmaf(-lk, lv[u], d[m]);
+                    a[m] = fmaf(-a[k], lv[u], a[m]);
+                }
+            }
         }
     }
 #pragma unroll
@@ -403,20 +419,22 @@ __device__ __noinline__ void chb_update(int W_o, int P_o, int j0, int nr, int nb
 }
 
 __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* Dinv, int n, int b, float* ws,
-                                     float* Rf, float* Rb, int RECE) {
+                                     float* Rf, float* Rb, int RECE, bool full) {
     const int nb = b + 1;
     const int tid = threadIdx.x, warp = tid >> 5;
     float* W = ws;
     float* P = W + (size_t)CHB_R * nb;   // P[k * CHB_RP + i'] = L(j0 + 32 + i', j0 + k)
     float* Z = P + 32 * CHB_RP;          // panel q: Z[(q & 1) * 1056 + i * 33 + c] = (L11^-1)(i, c)
     float* Li = Z + 2 * 32 * 33;         // 1/L_jj of panels of even / odd index
+    float* cb = Li + 64;                 // per panel warp, two buffers of the current column of L11
     // offsets (floats) of the workspace parts in the dynamic shared memory, for the panel bodies
     extern __shared__ float chb_dyn[];
-    const int o_W = (int)(W - chb_dyn), o_P = (int)(P - chb_dyn), o_Z = (int)(Z - chb_dyn), o_Li = (int)(Li - chb_dyn);
+    const int o_W = (int)(W - chb_dyn), o_P = (int)(P - chb_dyn), o_Z = (int)(Z - chb_dyn), o_Li = (int)(Li - chb_dyn),
+              o_cb = (int)(cb - chb_dyn);
     __shared__ int bad;
     if (tid == 0) bad = 0;
     // rows i < b of the row band have no columns j < 0
-    for (int idx = tid; idx < min(b, n) * b; idx += 256) {
+    for (int idx = tid; full && idx < min(b, n) * b; idx += 256) {
         const int i = idx / b, c = idx - i * b;
         if (c < b - i) Lr[(size_t)i * nb + c] = 0.f;
     }
@@ -439,17 +457,18 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
         const int j0 = 32 * q, jb = min(32, n - j0), t = tid - t0;
         const float* li = Li + (q & 1) * 32;
         const float* Zq = Z + (q & 1) * 32 * 33;
-        for (int k = 0; k < jb; ++k) {   // column band, contiguous
+        for (int k = 0; full && k < jb; ++k) {   // column band, contiguous
             const float* src = chb_col(W, j0 + k, nb);
             float* dst = Ac + (size_t)(j0 + k) * nb;
             for (int r = t; r < nb; r += nthr) dst[r] = (j0 + k + r < n) ? src[r] : 0.f;
         }
         const int rows = min(n, j0 + 32 + b) - j0;
-        for (int idx = t; idx < rows * 32; idx += nthr) {   // row band and backward records, j fastest
+        // row band and backward records, j fastest (records only: the rows below the block)
+        for (int idx = t + (full ? 0 : 32 * FSE_BLK); idx < rows * 32; idx += nthr) {
             const int ip = idx >> 5, k = idx & 31, i = j0 + ip, j = j0 + k, r = ip - k;
             if (k >= jb || r < 0 || r > b) continue;
             const float v = chb_col(W, j, nb)[r];
-            Lr[(size_t)i * nb + (b - r)] = v;
+            if (full) Lr[(size_t)i * nb + (b - r)] = v;
             if (Rb && ip >= 32) Rb[(size_t)q * RECE + (ip - 32) * FSE_BLK + k] = v;
         }
         if (Rf) {
@@ -463,13 +482,13 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
                 }
             }
         }
-        for (int k = t; k < jb; k += nthr) Linv[j0 + k] = li[k];
+        for (int k = t; full && k < jb; k += nthr) Linv[j0 + k] = li[k];
         float* D = Dinv + (size_t)q * FSE_BLK * FSE_BLK;
         const int dofs = RECE - FSE_BLK * FSE_BLK;
         for (int idx = t; idx < FSE_BLK * FSE_BLK; idx += nthr) {
             const int i = idx >> 5, c = idx & 31;
             const float z = Zq[i * 33 + c];
-            D[idx] = z;
+            if (full) D[idx] = z;
             if (Rf && Rb) {
                 Rb[(size_t)q * RECE + dofs + idx] = z;                 // backward record: Dinv
                 Rf[(size_t)q * RECE + dofs + c * FSE_BLK + i] = z;     // forward record: Dinv^T
@@ -485,7 +504,7 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
         const int j0 = 32 * p, jb = min(32, n - j0);
         const int nr = max(0, min(n, j0 + 32 + b) - (j0 + 32));   // rows of L21 (<= b)
         if (tid < 160) {
-            const bool ok = chb_panel(o_W, o_Li + (p & 1) * 32, o_P, o_Z + (p & 1) * 32 * 33, j0, jb, nr, b, nb);
+            const bool ok = chb_panel(o_W, o_Li + (p & 1) * 32, o_P, o_Z + (p & 1) * 32 * 33, o_cb, j0, jb, nr, b, nb);
             if (tid == 0 && !ok) bad = 1;
         } else if (p > 0) {
             write_panel(p - 1, 160, 96);
@@ -599,6 +618,10 @@ struct StateArgs {
     const void *cLc, *cLr, *cLinv, *cDinv;   // chord factor (regular steps)
     void *oLc, *oLr, *oLinv, *oDinv;         // factor of K_eff at the new state
     void *oRf, *oRb;                         // its block records for the tangent solves
+    const void *cRf, *cRb;                   // records of the chord factor (panel factor: the chord
+                                             // solves read them instead of the bands)
+    int full_factor;                         // panel factor: also write the bands, 1/L_jj and the block
+                                             // inverses (read by the tensor-core records)
     int RECE;
     int chol_blk;       // factor K_eff by 32-column panels (FP32, b <= 96)
     int *status, *iters, *nref;
@@ -609,7 +632,7 @@ struct StateArgs {
 template <typename T, bool BLK>
 __device__ int band_factor(const StateArgs& A, T* Ac, T* Lr, T* Linv, T* Dinv, T* wnd, T* stg, T* Rf, T* Rb) {
     if constexpr (BLK) {
-        return cta_band_cholesky_blk(Ac, Lr, Linv, Dinv, A.n, A.b, wnd, Rf, Rb, A.RECE);
+        return cta_band_cholesky_blk(Ac, Lr, Linv, Dinv, A.n, A.b, wnd, Rf, Rb, A.RECE, A.full_factor != 0);
     }
     const int bad = band_cholesky<T>(Ac, Lr, Linv, A.n, A.b, wnd, stg, Rf, Rb, A.RECE);
     if (!bad) cta_diag_inverses<T>(Lr, Linv, A.n, A.b, A.nblk, Dinv, wnd, Rf, Rb, A.RECE);
@@ -819,6 +842,98 @@ __device__ void cta_blocked_solve(const T* __restrict__ Lc, const T* __restrict_
     __syncthreads();
 }
 
+// The same solve for the panel factor (FP32, b <= 96), from the tangent-solve records of the
+// factor: forward record of block B [L(i0 + r, i0 - b + c) at c * 32 + r | Dinv^T at
+// (bpad + k) * 32 + r], backward record [L(i0 + 32 + c, i0 + r) at c * 32 + r | Dinv]; entries
+// outside the band are zero there.  Each block's record (RECE floats) is copied to shared memory
+// by 16-byte cp.async while the previous block computes, into rows padded to 36 floats (ws: two
+// such buffers): the 32 lanes of a warp (4 rows r x 8 record rows c) then read 32 different
+// banks, 4 c + r.
+__device__ void cta_record_solve(const float* __restrict__ Rf, const float* __restrict__ Rb, int RECE, int n, int b,
+                                 int nblk, double* r, float* y, float* tmp, float* ws) {
+    constexpr int MC = 12;     // band entries per lane (b <= 96)
+    constexpr int MAXU = 4;    // 16-byte chunks per thread (RECE <= (96 + 32) * 32 = 4 * 4 * 256)
+    constexpr int RP = 36;
+    const int tid = threadIdx.x, row = tid >> 3, l8 = tid & 7;   // 32 rows x 8 lanes
+    const int nrr = RECE / FSE_BLK, dr = nrr - FSE_BLK;          // record rows; first row of the block inverse
+    float* rs[2] = {ws, ws + nrr * RP};
+    auto fetch = [&](const float* R, float* d) {   // record R into the padded buffer d
+#pragma unroll
+        for (int u = 0; u < MAXU; ++u) {
+            const int ch = tid + 256 * u;   // floats 4 ch .. 4 ch + 3: record row ch / 8
+            if (4 * ch < RECE) cp_async16(d + (ch >> 3) * RP + 4 * (ch & 7), R + 4 * ch, 16);
+        }
+        cp_async_commit();
+    };
+    for (int i = tid; i < n; i += blockDim.x) y[i] = float(r[i]);
+    // forward: y_B = Dinv_B (r_B - L_{B,<} y_<)
+    fetch(Rf, rs[0]);
+    cp_async_wait0();
+    __syncthreads();
+    for (int B = 0; B < nblk; ++B) {
+        const int i0 = B * FSE_BLK, i = i0 + row;
+        const float* R = rs[B & 1];
+        if (B + 1 < nblk) fetch(Rf + (size_t)(B + 1) * RECE, rs[(B + 1) & 1]);   // last read at block B - 1
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int c = l8 + 8 * q, j = i0 - b + c;
+            if (c < b && j >= 0) part += R[c * RP + row] * y[j];
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        if (l8 == 0) tmp[row] = (i < n) ? y[i] - part : 0.f;
+        __syncthreads();
+        float yv = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = l8 + 8 * q;
+            yv += R[(dr + k) * RP + row] * tmp[k];
+        }
+        yv += __shfl_xor_sync(0xffffffffu, yv, 4);
+        yv += __shfl_xor_sync(0xffffffffu, yv, 2);
+        yv += __shfl_xor_sync(0xffffffffu, yv, 1);
+        if (l8 == 0 && i < n) y[i] = yv;
+        cp_async_wait0();
+        __syncthreads();
+    }
+    // backward: x_B = Dinv_B^T (y_B - L_{>,B}^T x_>)
+    fetch(Rb + (size_t)(nblk - 1) * RECE, rs[0]);
+    cp_async_wait0();
+    __syncthreads();
+    for (int q2 = 0; q2 < nblk; ++q2) {
+        const int B = nblk - 1 - q2, i0 = B * FSE_BLK, i = i0 + row;
+        const float* R = rs[q2 & 1];
+        if (B > 0) fetch(Rb + (size_t)(B - 1) * RECE, rs[(q2 + 1) & 1]);
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int c = l8 + 8 * q, k = i0 + FSE_BLK + c;
+            if (c < b && k < n) part += R[c * RP + row] * y[k];
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        if (l8 == 0) tmp[row] = (i < n) ? y[i] - part : 0.f;
+        __syncthreads();
+        float xv = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = row + l8 + 8 * q;
+            if (k < FSE_BLK) xv += R[(dr + k) * RP + row] * tmp[k];
+        }
+        xv += __shfl_xor_sync(0xffffffffu, xv, 4);
+        xv += __shfl_xor_sync(0xffffffffu, xv, 2);
+        xv += __shfl_xor_sync(0xffffffffu, xv, 1);
+        if (l8 == 0 && i < n) y[i] = xv;
+        cp_async_wait0();
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) r[i] = (double)y[i];
+    __syncthreads();
+}
+
 // Single-warp banded solve of the FP64 mass factor (setup-time layouts), used once per
 // evaluation for the consistent initial acceleration.
 __device__ void warp_band_solve_fp64(const double* __restrict__ Lc, const double* __restrict__ Lr,
@@ -923,6 +1038,9 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
         const T* cLc = reinterpret_cast<const T*>(A.cLc) + foff;
         const T* cLr = reinterpret_cast<const T*>(A.cLr) + foff;
         const T* cDi = reinterpret_cast<const T*>(A.cDinv) + doff;
+        const size_t roff = (size_t)s * A.nblk * A.RECE;
+        const T* cRf = BLK ? reinterpret_cast<const T*>(A.cRf) + roff : nullptr;
+        const T* cRb = BLK ? reinterpret_cast<const T*>(A.cRb) + roff : nullptr;
         // b = e_{k+1} + w^2 M (a0 q + a1 u + a) + w D (a2 q + u)   (Eq. E7)
         for (int i = tid; i < n; i += nt) {
             sr[i] = A.a0c * sq[i] + A.a1c * su[i] + sa[i];
@@ -949,7 +1067,10 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             __syncthreads();
             vel_iterate();
             add_fnl(A, sqn, sv, sr);
-            cta_blocked_solve<T>(cLc, cLr, cDi, n, b, A.nblk, sr, ysol, tmp);
+            if constexpr (BLK)
+                cta_record_solve(cRf, cRb, A.RECE, n, b, A.nblk, sr, ysol, tmp, wnd);
+            else
+                cta_blocked_solve<T>(cLc, cLr, cDi, n, b, A.nblk, sr, ysol, tmp);
             double dmax = 0.0, qmax = 0.0;
             for (int i = tid; i < n; i += nt) {
                 const double v = sqn[i] - sr[i];
@@ -983,6 +1104,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
                 cLc = oLc;
                 cLr = oLr;
                 cDi = oDi;
+                cRf = oRf;
+                cRb = oRb;
             }
             prev = dmax;
         }
@@ -1177,6 +1300,9 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     const size_t rsz = (size_t)p.N * p.nblk * p.RECE * tsz;
     A.oRf = (char*)c->d.Rf + fo * rsz;
     A.oRb = (char*)c->d.Rb + fo * rsz;
+    A.cRf = (char*)c->d.Rf + fi * rsz;
+    A.cRb = (char*)c->d.Rb + fi * rsz;
+    A.full_factor = use_tc(c) ? 1 : 0;
     A.RECE = p.RECE;
     A.chol_blk = p.chol_blk;
     A.status = c->d.status;
