@@ -141,7 +141,7 @@ static void free_ctx(fse_ctx* c) {
                     c->d.ktab, c->d.LMc, c->d.LMr, c->d.LMinv, c->d.q, c->d.u, c->d.a, c->d.zb,
                     c->d.Lc, c->d.Lr, c->d.Linv, c->d.Dinv, c->d.Rf, c->d.Rb, c->d.Tf, c->d.Tb, c->d.X, c->d.V, c->d.Y, c->d.Z0, c->d.R,
                     c->d.vec, c->d.vec2, c->d.yb, c->d.status, c->d.iters, c->d.nref, c->d.flag, c->Jd, c->piv, c->kry, c->kdot,
-                    c->ht, c->unk};
+                    c->ht, c->unk, c->d.Sband, c->d.ktc_ptr, c->d.ktc_e, c->d.ktc_c, c->d.ktc_r};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -513,6 +513,33 @@ static int setup_impl(const fse_model* m, const fse_opts* o, long long s_begin, 
     A(&c->d.cs_A, (size_t)p.nnz * tsz);
     A(&c->d.cs_B, (size_t)p.nnz * tsz);
     A(&c->d.kt_ptr, (size_t)(n + 1) * 4);
+    // panel factor: K_t entries of the lower triangle grouped by column
+    std::vector<int> ktc_ptr(n + 1, 0), ktc_e, ktc_c, ktc_r;
+    if (p.chol_blk) {
+        for (int i = 0; i < n; ++i)
+            for (int e = kptr[i]; e < kptr[i + 1]; ++e)
+                if (kcol[e] <= i) ++ktc_ptr[kcol[e] + 1];
+        for (int j = 0; j < n; ++j) ktc_ptr[j + 1] += ktc_ptr[j];
+        const int nl = ktc_ptr[n];
+        ktc_e.assign(std::max(1, nl), 0);
+        ktc_c.assign(std::max(1, nl), 0);
+        ktc_r.assign(std::max(1, nl), 0);
+        std::vector<int> fill(ktc_ptr.begin(), ktc_ptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int e = kptr[i]; e < kptr[i + 1]; ++e) {
+                const int j = kcol[e];
+                if (j > i) continue;
+                const int k = fill[j]++;
+                ktc_e[k] = e;
+                ktc_c[k] = j;
+                ktc_r[k] = i - j;
+            }
+        A(&c->d.Sband, (size_t)n * nb * 4);
+        A(&c->d.ktc_ptr, (size_t)(n + 1) * 4);
+        A(&c->d.ktc_e, ktc_e.size() * 4);
+        A(&c->d.ktc_c, ktc_c.size() * 4);
+        A(&c->d.ktc_r, ktc_r.size() * 4);
+    }
     A(&c->d.kt_col, (size_t)std::max(1, p.nnz_kt) * 4);
     A(&c->d.kt_soff, (size_t)(p.nnz_kt + 1) * 4);
     A(&c->d.kt_src, (size_t)std::max<size_t>(1, ksrc.size()) * 4);
@@ -591,6 +618,12 @@ static int setup_impl(const fse_model* m, const fse_opts* o, long long s_begin, 
     cudaMemcpyAsync(c->d.cs_d, cd.data(), cd.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.cs_k, ck.data(), ck.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->d.kt_ptr, kptr.data(), kptr.size() * 4, cudaMemcpyHostToDevice, st);
+    if (p.chol_blk) {
+        cudaMemcpyAsync(c->d.ktc_ptr, ktc_ptr.data(), ktc_ptr.size() * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d.ktc_e, ktc_e.data(), ktc_e.size() * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d.ktc_c, ktc_c.data(), ktc_c.size() * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->d.ktc_r, ktc_r.data(), ktc_r.size() * 4, cudaMemcpyHostToDevice, st);
+    }
     if (p.nnz_kt > 0) {
         cudaMemcpyAsync(c->d.kt_col, kcol.data(), kcol.size() * 4, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(c->d.kt_src, ksrc.data(), ksrc.size() * 4, cudaMemcpyHostToDevice, st);

@@ -56,6 +56,11 @@ struct Dev {
     // CSR of the K_t pattern and the element-tangent sources of each entry
     int* kt_ptr = nullptr;
     int* kt_col = nullptr;
+    // panel factor: the lower band of S in FP32 (column band, shared by all trajectories, rebuilt
+    // with the operators) and the K_t entries of the lower triangle by column: entry ktc_e[k] of the
+    // CSR, column ktc_c[k], row offset ktc_r[k], k in ktc_ptr[j] .. ktc_ptr[j + 1]
+    void* Sband = nullptr;
+    int *ktc_ptr = nullptr, *ktc_e = nullptr, *ktc_c = nullptr, *ktc_r = nullptr;
     int* kt_slot = nullptr;  // kt_col mod RW
     // row groups of the right-hand-side kernel (rows with identical column patterns)
     int* g_pass = nullptr;   // 8 per pass: rows to stage, entry range, K_t slice (first, count), first group

@@ -76,6 +76,17 @@ __global__ void k_build_ops(int nnz, double cm, double cd, double cb, const doub
     }
 }
 
+// lower column band of S in FP32 for the panel factor: Sband[j (b + 1) + i - j] = S_ij, i >= j (zero
+// elsewhere: the caller clears it first); one thread per row
+__global__ void k_sband(int n, int nb, const int* __restrict__ ptr, const int* __restrict__ col,
+                        const double* __restrict__ S, float* Sband) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+            const int j = col[e];
+            if (j <= i) Sband[(size_t)j * nb + (i - j)] = float(S[e]);
+        }
+}
+
 // ----------------------------------------------------------------------------
 // banded Cholesky inside one CTA: column band Ac (global, in place) -> Lc, Lr, Linv
 // ----------------------------------------------------------------------------
@@ -297,8 +308,9 @@ __device__ int cta_band_cholesky_r(T* Ac, T* Lr, T* Linv, int n, int b, T* colbu
 // of L11^-1).  The trailing update (4 x 4 register tiles, all warps) and two CTA barriers come
 // once per panel, against one barrier per column in the unblocked form.  Warps 5-7 write the
 // previous panel's columns of L out (column band, row band, Linv, block inverse and the tangent-
-// solve records) while the panel is factored; warps 4-7 then stage from the assembled band the
-// columns that the next panel updates first.
+// solve records) while the panel is factored; warps 4-7 then stage the columns that the next panel
+// updates first, as the band of S (one FP32 copy for all trajectories) plus the trajectory's K_t
+// and C_t entries of those columns: K_eff is never assembled in global memory.
 // Shared workspace (floats): a ring of CHB_R columns of the band (column c in slot c mod CHB_R,
 // entry c + r at r), L21 transposed [32][CHB_RP], L11^-1 of two panels [2][32][33], 1/L_jj of
 // two panels, per panel warp two buffers of the current column of L11.
@@ -307,6 +319,16 @@ constexpr int CHB_RP = 100;   // row pitch of the transposed L21 (>= b, a multip
 __host__ __device__ constexpr size_t chol_blk_floats(int nb) {
     return (size_t)CHB_R * nb + 32 * CHB_RP + 2 * 32 * 33 + 64 + 5 * 64;
 }
+
+// where the panel factor takes K_eff = S + K_t + w (2/Delta) C_t from: the lower band of S (FP32,
+// all trajectories), the lower K_t entries by column, this trajectory's K_t and C_t values
+// (ct null without velocity-dependent elements) and w (2/Delta)
+struct ChbSource {
+    const float* Sband;
+    const int *ktc_ptr, *ktc_e, *ktc_c, *ktc_r;
+    const float *kt, *ct;
+    float wa;
+};
 
 // column c of the ring: W + (c mod CHB_R) nb
 __device__ __forceinline__ float* chb_col(float* W, int c, int nb) { return W + (size_t)(c % CHB_R) * nb; }
@@ -419,7 +441,7 @@ __device__ __noinline__ void chb_update(int W_o, int P_o, int j0, int nr, int nb
 }
 
 __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* Dinv, int n, int b, float* ws,
-                                     float* Rf, float* Rb, int RECE, bool full) {
+                                     float* Rf, float* Rb, int RECE, bool full, const ChbSource& src) {
     const int nb = b + 1;
     const int tid = threadIdx.x, warp = tid >> 5;
     float* W = ws;
@@ -438,19 +460,41 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
         const int i = idx / b, c = idx - i * b;
         if (c < b - i) Lr[(size_t)i * nb + c] = 0.f;
     }
-    // columns [c0, c1) of the assembled band into the ring, zero past n; threads t0 .. t0 + nthr - 1
+    // columns [c0, c1) of K_eff into the ring (zero past n): the band of S, then this trajectory's
+    // K_t (and C_t) entries of those columns; threads t0 .. t0 + nthr - 1, either the whole CTA or
+    // warps 4-7, which synchronise on named barrier 1 between the two
     auto stage = [&](int c0, int c1, int t0, int nthr) {
-        for (int c = c0; c < c1; ++c) {
-            float* d = chb_col(W, c, nb);
-            const float* g = Ac + (size_t)c * nb;
-            for (int r = tid - t0; r < nb; r += nthr) {
-                if (c + r < n)
-                    cp_async_elem(d + r, g + r);
-                else
-                    d[r] = 0.f;
+        const int cnt = max(0, c1 - c0) * nb;
+        const float* g = src.Sband + (size_t)c0 * nb;
+        for (int base = tid - t0; base < cnt; base += 4 * nthr) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * nthr;
+                v[u] = idx < cnt ? g[idx] : 0.f;   // entries past row n are zero in the band of S
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * nthr;
+                if (idx < cnt) {
+                    const int q = idx / nb;
+                    chb_col(W, c0 + q, nb)[idx - q * nb] = v[u];
+                }
             }
         }
-        cp_async_commit();
+        if (nthr == 256)
+            __syncthreads();
+        else
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");
+        if (c1 > c0) {
+            const int k1 = src.ktc_ptr[c1];
+            for (int k = src.ktc_ptr[c0] + tid - t0; k < k1; k += nthr) {
+                const int e = src.ktc_e[k];
+                float v = src.kt[e];
+                if (src.ct) v += src.wa * src.ct[e];
+                chb_col(W, src.ktc_c[k], nb)[src.ktc_r[k]] += v;
+            }
+        }
     };
     // write panel q's columns of L out of the ring; threads t0 .. t0 + nthr - 1
     auto write_panel = [&](int q, int t0, int nthr) {
@@ -496,7 +540,6 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
         }
     };
     stage(0, min(n, 32 + b), 0, 256);
-    cp_async_wait0();
     __syncthreads();
     const int npan = (n + FSE_BLK - 1) / FSE_BLK;
     int p = 0;
@@ -517,11 +560,9 @@ __device__ int cta_band_cholesky_blk(float* Ac, float* Lr, float* Linv, float* D
             stage(min(n, c0), min(n, c0 + 32), 128, 128);
         }
         chb_update(o_W, o_P, j0, nr, nb);
-        cp_async_wait0();
         __syncthreads();
     }
     if (p == npan) write_panel(npan - 1, 0, 256);
-    cp_async_wait0();
     __syncthreads();
     return bad;
 }
@@ -622,6 +663,8 @@ struct StateArgs {
                                              // solves read them instead of the bands)
     int full_factor;                         // panel factor: also write the bands, 1/L_jj and the block
                                              // inverses (read by the tensor-core records)
+    const float* Sband;                      // panel factor: lower band of S (all trajectories)
+    const int *ktc_ptr, *ktc_e, *ktc_c, *ktc_r;   // ... and the lower K_t entries by column
     int RECE;
     int chol_blk;       // factor K_eff by 32-column panels (FP32, b <= 96)
     int *status, *iters, *nref;
@@ -630,9 +673,11 @@ struct StateArgs {
 // factor of K_eff (column band Ac in place, row band, 1/L_jj, diagonal-block inverses and the
 // tangent-solve records); nonzero on a non-positive or non-finite pivot
 template <typename T, bool BLK>
-__device__ int band_factor(const StateArgs& A, T* Ac, T* Lr, T* Linv, T* Dinv, T* wnd, T* stg, T* Rf, T* Rb) {
+__device__ int band_factor(const StateArgs& A, T* Ac, T* Lr, T* Linv, T* Dinv, T* wnd, T* stg, T* Rf, T* Rb,
+                           const T* kt = nullptr, const T* ct = nullptr) {
     if constexpr (BLK) {
-        return cta_band_cholesky_blk(Ac, Lr, Linv, Dinv, A.n, A.b, wnd, Rf, Rb, A.RECE, A.full_factor != 0);
+        const ChbSource src{A.Sband, A.ktc_ptr, A.ktc_e, A.ktc_c, A.ktc_r, kt, ct, float(A.w * A.a2c)};
+        return cta_band_cholesky_blk(Ac, Lr, Linv, Dinv, A.n, A.b, wnd, Rf, Rb, A.RECE, A.full_factor != 0, src);
     }
     const int bad = band_cholesky<T>(Ac, Lr, Linv, A.n, A.b, wnd, stg, Rf, Rb, A.RECE);
     if (!bad) cta_diag_inverses<T>(Lr, Linv, A.n, A.b, A.nblk, Dinv, wnd, Rf, Rb, A.RECE);
@@ -666,7 +711,9 @@ __device__ void add_fnl(const StateArgs& A, const double* q, const double* qd, d
 
 // Ac = lower column band of K_eff = S + K_t(q, qdot) + w (2/Delta) C_t(q, qdot) (type T), kt_out =
 // K_t values on its CSR pattern and, with velocity-dependent elements, ct_out = C_t values on it.
-template <typename T>
+// BAND = false (panel factor): kt_out and ct_out only; the factor stages K_eff itself from the
+// band of S and these values.
+template <typename T, bool BAND = true>
 __device__ void assemble_keff(const StateArgs& A, int s, const double* q, const double* qd, T* Ac, T* kt_out,
                               T* ct_out) {
     const int n = A.n, b = A.b, nb = b + 1;
@@ -677,13 +724,15 @@ __device__ void assemble_keff(const StateArgs& A, int s, const double* q, const 
         elem_eval(A.el_type[el], A.el_dof + 6 * el, A.el_p + 6 * el, q, qd, fe, ke + (size_t)el * 36,
                   ce ? ce + (size_t)el * 36 : nullptr);
     }
-    for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) Ac[idx] = T(0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int e1 = A.cs_ptr[i + 1];
-        for (int e = A.cs_ptr[i]; e < e1; ++e) {
-            const int j = A.cs_col[e];
-            if (j <= i) Ac[(size_t)j * nb + (i - j)] = T(A.cs_s[e]);
+    if constexpr (BAND) {
+        for (int idx = threadIdx.x; idx < n * nb; idx += blockDim.x) Ac[idx] = T(0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int e1 = A.cs_ptr[i + 1];
+            for (int e = A.cs_ptr[i]; e < e1; ++e) {
+                const int j = A.cs_col[e];
+                if (j <= i) Ac[(size_t)j * nb + (i - j)] = T(A.cs_s[e]);
+            }
         }
     }
     __syncthreads();
@@ -700,7 +749,7 @@ __device__ void assemble_keff(const StateArgs& A, int s, const double* q, const 
                 v += A.w * A.a2c * vc;   // d u / d q = 2 / Delta, d qdot / d u = w
             }
             const int j = A.kt_col[e];
-            if (j <= i) {
+            if (BAND && j <= i) {
                 const size_t o = (size_t)j * nb + (i - j);
                 Ac[o] = T((double)Ac[o] + v);
             }
@@ -1094,8 +1143,8 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
             if (prev > 0.0 && dmax > 0.1 * prev && it + 1 < A.maxit && allow) {
                 ++nref;
                 vel_iterate();
-                assemble_keff<T>(A, s, sqn, sv, oLc, kt_out, ct_out);
-                if (band_factor<T, BLK>(A, oLc, oLr, oLi, oDi, wnd, stg, oRf, oRb)) {
+                assemble_keff<T, !BLK>(A, s, sqn, sv, oLc, kt_out, ct_out);
+                if (band_factor<T, BLK>(A, oLc, oLr, oLi, oDi, wnd, stg, oRf, oRb, kt_out, ct_out)) {
                     if (tid == 0) s_stat = FSE_ENONPOS_PIVOT;
                     ++it;
                     break;
@@ -1137,7 +1186,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
     int bad = 0;
     if (A.refactor) {
         vel_state();
-        assemble_keff<T>(A, s, sq, sv, oLc, kt_out, ct_out);
+        assemble_keff<T, !BLK>(A, s, sq, sv, oLc, kt_out, ct_out);
         if (A.has_vel && !A.init) {
             // velocity-dependent elements add - C_t(k+1) u_{k+1} - C_t(k) u_k to the w_1 column
             // (d f / d w_1 = C_t u at both ends of the step); sb holds u_k + u_{k+1}, su u_{k+1}
@@ -1154,7 +1203,7 @@ __global__ void __launch_bounds__(256) k_state(StateArgs A) {
                 rom[i] = T((double)rom[i] - acc);
             }
         }
-        bad = band_factor<T, BLK>(A, oLc, oLr, oLi, oDi, wnd, stg, oRf, oRb);
+        bad = band_factor<T, BLK>(A, oLc, oLr, oLi, oDi, wnd, stg, oRf, oRb, kt_out, ct_out);
     }
     if (tid == 0) {
         if (bad && s_stat == 0) s_stat = FSE_ENONPOS_PIVOT;
@@ -1204,6 +1253,12 @@ void launch_build_ops(fse_ctx* c, double w) {
     else
         k_build_ops<double><<<g, 256, 0, c->stream>>>(p.nnz, cm, cd, cb, c->d.cs_m, c->d.cs_d, c->d.cs_k,
                                                       c->d.cs_s, (double*)c->d.cs_A, (double*)c->d.cs_B);
+    if (p.chol_blk) {
+        const int nb = p.b + 1;
+        cudaMemsetAsync(c->d.Sband, 0, (size_t)p.n * nb * 4, c->stream);
+        k_sband<<<nblocks(p.n, 128), 128, 0, c->stream>>>(p.n, nb, c->d.cs_ptr, c->d.cs_col, c->d.cs_s,
+                                                          (float*)c->d.Sband);
+    }
 }
 
 int launch_factor_M(fse_ctx* c) {
@@ -1303,6 +1358,11 @@ static StateArgs make_state_args(fse_ctx* c, double w, int init, int k) {
     A.cRf = (char*)c->d.Rf + fi * rsz;
     A.cRb = (char*)c->d.Rb + fi * rsz;
     A.full_factor = use_tc(c) ? 1 : 0;
+    A.Sband = (const float*)c->d.Sband;
+    A.ktc_ptr = c->d.ktc_ptr;
+    A.ktc_e = c->d.ktc_e;
+    A.ktc_c = c->d.ktc_c;
+    A.ktc_r = c->d.ktc_r;
     A.RECE = p.RECE;
     A.chol_blk = p.chol_blk;
     A.status = c->d.status;
