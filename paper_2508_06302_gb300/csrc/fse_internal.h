@@ -96,7 +96,10 @@ struct Dev {
     double* u = nullptr;
     double* a = nullptr;
     double* zb = nullptr;    // N x 2n  (start / end points)
-    // factor of K_eff (sensitivity precision), FSE_NBUF_F buffers
+    // factor of K_eff (sensitivity precision), FSE_NBUF_F buffers.  The panel factor (chol_blk)
+    // writes the bands, Linv and Dinv only while the tensor-core solves are selected (their records
+    // are built from Lr and Dinv); it always writes Rf and Rb, which its chord solves read.  Lc is
+    // also the assembled K_eff that the column-by-column factors take as input.
     void* Lc = nullptr;      // NBUF x N x n x (b+1)
     void* Lr = nullptr;
     void* Linv = nullptr;    // NBUF x N x n
