@@ -214,6 +214,23 @@ def step_work(m, N, band, ld, prec_bytes):
     }
 
 
+def step_rates(work, traj_steps_per_s, N, hbm_gbs, fp64_tflops=None, bf16_tflops=None):
+    """Whole-step rates of the tangent propagation from the measured throughput: the algorithmic
+    bytes and flops of the three sensitivity kernels per Newmark step of all N trajectories
+    (`step_work`), over the time of one such step, against the HBM peak and as multiples of the
+    FP64 and BF16 tensor peaks (the tangent flops are FP32, so the FP64 ratio exceeds 1; the state
+    step's FP64 work, the DFTs and the outer solves are not counted)."""
+    t = N / traj_steps_per_s
+    by = sum(v[1] for v in work.values())
+    fl = sum(v[0] for v in work.values())
+    gbs = by / t / 1e9
+    tf = fl / t / 1e12
+    return {"tangent_bytes_per_step": by, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_gbs,
+            "tangent_flops_per_step": fl, "tflops": tf,
+            "vs_fp64_peak": tf / fp64_tflops if fp64_tflops else None,
+            "vs_bf16_peak": tf / bf16_tflops if bf16_tflops else None}
+
+
 def kernel_source_hash(source="fse_sens.cu"):
     """Hash of a kernel file's device code: the .cu file up to its host launchers, plus the device
     helpers of fse_common.cuh, with // comments and whitespace removed (a change in host code or
@@ -655,7 +672,11 @@ def main():
         # sensitivity kernels), join, DFT + residual
         # (+1 per step: the factor records of the tensor-core solves)
         "gpu_launches": args.steps * ((5 if tc else 4) * n_newmark + 6),
-        "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "peaks_source": src,
+        "roofline": roof,
+        # per GPU (each rank integrates its own N trajectories)
+        "step_rates": step_rates(work, value / world, N, hbm_peak, (peaks_gemm or {}).get("fp64_tflops"),
+                                 peaks.get("bf16_tflops")),
+        "clocks": clk, "cpu_baseline": cpu, "peaks_source": src,
         "peaks_measured": peaks_gemm,
         "alu_peak_derived_tflops": alu_derived,
     }
