@@ -636,19 +636,26 @@ def main():
                 "peak_source": psrc}
     batch = None
     if args.batch:
-        batch = batch_points(fse, local)
+        try:
+            batch = batch_points(fse, local)
+        except Exception as exc:
+            batch = {"error": "%s: %s" % (type(exc).__name__, exc)}
     cont = None
     n_points = args.points if args.points >= 0 else (8 if world == 1 else 0)
     if n_points > 0:
         cont = {}
-        for p in (["secant", "mlp"] if args.predictor == "both" else [args.predictor]):
-            cont[p] = continuation_points(fse, ctx, wl, n_points, p, local)
-        omegas, Zc, pts_c = continuation_points.last
-        k64 = args.fp64_points if args.fp64_points >= 0 else 1
-        if k64 > 0:
-            cont["fp64_plain"] = fp64_points(fse, wl, omegas, Zc, pts_c, min(k64, n_points), local)
-            best = max(v["points_per_s"] or 0.0 for k, v in cont.items() if k != "fp64_plain")
-            cont["vs_fp64_plain"] = best / cont["fp64_plain"]["points_per_s"]
+        # a sweep that fails is reported in the line; the timed evaluation above stands
+        try:
+            for p in (["secant", "mlp"] if args.predictor == "both" else [args.predictor]):
+                cont[p] = continuation_points(fse, ctx, wl, n_points, p, local)
+            omegas, Zc, pts_c = continuation_points.last
+            k64 = args.fp64_points if args.fp64_points >= 0 else 1
+            if k64 > 0:
+                cont["fp64_plain"] = fp64_points(fse, wl, omegas, Zc, pts_c, min(k64, n_points), local)
+                best = max(v["points_per_s"] or 0.0 for k, v in cont.items() if k != "fp64_plain")
+                cont["vs_fp64_plain"] = best / cont["fp64_plain"]["points_per_s"]
+        except Exception as exc:
+            cont["error"] = "%s: %s" % (type(exc).__name__, exc)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
